@@ -1,0 +1,218 @@
+/*
+ * rbmf.h - C ABI of the GB300 (sm_103a) hierarchical reduced-basis matched filter.
+ *
+ * Method: arXiv:2110.13115 (Dhurkunde, Fehrmann, Nitz), "A hierarchical approach to
+ * matched filtering using a reduced basis".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - A block holds n samples at fs Hz (n a power of two, 2^10 <= n <= 2^20); df = fs/n.
+ *    Frequencies f_j = j df, j in [0, n/2]. Only 0 < j < n/2 enters any sum
+ *    (one-sided matched filter of Eq. (1); DC and Nyquist excluded).
+ *  - Blocks overlap by n/2 (Sec. III.F): only block samples m in [n/2, n) are valid and
+ *    reported. Trigger sample indices are sample_offset + m.
+ *  - Whitened coordinates: x_hat[j] = sqrt(4 df / S_j) x(f_j), with x(f) = dt * DFT(x).
+ *    In them the inner product <a|b> of Eq. (1) is sum_j a_hat[j] conj(b_hat[j]).
+ *  - Complex arrays are interleaved float pairs (re, im), C order as stated per argument.
+ *  - Pointers are DEVICE pointers unless the argument says "host". All buffers are owned
+ *    by the caller; the library allocates no device memory: every call that needs scratch
+ *    space takes a caller-provided workspace of at least the size rb_filter_plan reports
+ *    (256-byte aligned).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Calls that return counts
+ *    (n_out) synchronise that stream before returning; the others only enqueue work.
+ *  - Every function returns RB_OK (0) or a negative RB_ERR_* code; nothing throws.
+ *    rb_strerror() names a code, rb_last_error_detail() describes the last failure on the
+ *    calling thread (a CUDA error string, which argument was rejected).
+ */
+#ifndef RBMF_H
+#define RBMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RB_OK = 0,
+  RB_ERR_BAD_INPUT = -1,   /* a descriptor field, size or pointer is invalid */
+  RB_ERR_OOM = -2,         /* the workspace passed is smaller than rb_filter_plan's size */
+  RB_ERR_OVERFLOW = -3,    /* an output or candidate list was too small; *n_out = required */
+  RB_ERR_TIMEOUT = -4,     /* a device-side bounded wait gave up */
+  RB_ERR_CUDA = -5,        /* a CUDA runtime call or launch failed */
+  RB_ERR_UNSUPPORTED = -6  /* valid request the build does not support (size, precision) */
+};
+
+/* Stage-1 reconstruction arithmetic (Sec. III.C first stage; precision study). */
+enum {
+  RB_PREC_FP32 = 0,        /* FP32 SIMT complex GEMM */
+  RB_PREC_FP16_SPLIT = 1,  /* tcgen05 FP16 operands split hi+lo, 3 MMAs, FP32 accumulate */
+  RB_PREC_BF16_SPLIT = 2,  /* tcgen05 BF16 operands split hi+lo, 3 MMAs, FP32 accumulate */
+  RB_PREC_FP16 = 3,        /* tcgen05 single FP16 operands, FP32 accumulate */
+  RB_PREC_BF16 = 4         /* tcgen05 single BF16 operands, FP32 accumulate */
+};
+
+/* One block's filtering parameters. */
+typedef struct rb_filter_desc {
+  double fs;              /* sample rate [Hz] */
+  int64_t n;              /* block length: power of two, 2^10..2^20 */
+  int32_t k;              /* basis vectors used (rows of rb_basis.vectors) */
+  int32_t n_templates;    /* T: rows of rb_basis.coeff */
+  int32_t w;              /* bin width in samples (Eq. 9): 1, 2, 4, 8 or 16 */
+  int32_t precision;      /* RB_PREC_* for the first stage */
+  float rho_i;            /* first-stage threshold on the bin-averaged SNR (Sec. III.C) */
+  float rho_ii;           /* second-stage threshold on the full-rate SNR (Sec. III.C) */
+  int64_t cand_capacity;  /* first-stage candidate slots kept in the workspace */
+  int64_t sample_offset;  /* global index of block sample 0 */
+  int32_t block_id;       /* copied into rb_trigger.block / rb_candidate.block */
+  int32_t reserved;       /* must be 0 */
+} rb_filter_desc;
+
+/* The reduced basis of a template bank (output of rb_build; caller-owned arrays). */
+typedef struct rb_basis {
+  int32_t k;              /* basis vectors stored */
+  int32_t n_templates;    /* T */
+  int64_t n;              /* block length the basis was built for */
+  const float* vectors;   /* [k][n/2] complex: p_k in whitened coordinates, orthonormal */
+  const float* coeff;     /* [T][k] complex: a_tk = <g_t|p_k> / sigma_t (SNR units, Eq. 7) */
+  const void* coeff_op;   /* packed first-stage operand from rb_pack_coeff (NULL for FP32) */
+  int32_t coeff_op_precision; /* RB_PREC_* coeff_op was packed for */
+  int32_t reserved;
+} rb_basis;
+
+/* A final trigger (Sec. III.C second stage; also the template method's triggers). */
+typedef struct rb_trigger {
+  int64_t sample;   /* sample_offset + block sample m of the window's arg-max */
+  int32_t tmpl;     /* template row */
+  int32_t block;    /* rb_filter_desc.block_id */
+  float snr;        /* rho = |z| / sigma */
+  float phase;      /* arg z in (-pi, pi] */
+} rb_trigger;       /* 24 bytes */
+
+/* A first-stage candidate: a (template, bin) whose bin-averaged SNR reached rho_I. */
+typedef struct rb_candidate {
+  int32_t tmpl;     /* template row */
+  int32_t bin;      /* bin index i of Eq. (9): samples [i w, i w + w) of the block */
+  float snr_avg;    /* |sum_k a_tk^* beta^avg_k[i]| */
+  int32_t block;    /* rb_filter_desc.block_id */
+} rb_candidate;     /* 16 bytes */
+
+/* Sizes derived from a descriptor (host-only, no CUDA call). */
+typedef struct rb_filter_sizes {
+  size_t workspace_bytes;   /* minimum workspace for rb_filter / rb_filter_plain / stage calls */
+  int64_t n_bins;           /* valid bins n/(2w) */
+  int32_t n1, n2;           /* four-step split n = n1 * n2 */
+  int32_t kp;               /* stage-1 contraction length 2k rounded up to 64 */
+  size_t coeff_op_bytes;    /* bytes rb_pack_coeff writes for desc->precision (0 for FP32) */
+} rb_filter_sizes;
+
+/* Name of a status code (static string). */
+const char* rb_strerror(int status);
+/* Details of the last failure on the calling thread (static per-thread buffer). */
+const char* rb_last_error_detail(void);
+/* Library version: major*10000 + minor*100 + patch. */
+int rb_version(void);
+
+/*
+ * rb_filter_plan - validate `desc` and report workspace size and layout parameters.
+ * Host only. Errors: RB_ERR_BAD_INPUT (n not a power of two in range, k < 1, T < 1,
+ * w not in {1,2,4,8,16}, w > n/2, thresholds negative or NaN, reserved != 0),
+ * RB_ERR_UNSUPPORTED (precision unknown).
+ */
+int rb_filter_plan(const rb_filter_desc* desc, rb_filter_sizes* out /* host */);
+
+/*
+ * rb_whiten - step a1: s_hat[j] = sqrt(4 df / S_j) * dt * DFT(strain)[j] for j in [0, n/2)
+ * (s_hat[0] = 0), by a forward Stockham FFT with the whitening fused into its last pass.
+ * Paper: Sec. III.C (first bullet; data FFT) and Sec. III.E (whitening by S_n^{-1/2}).
+ *   strain: [n] float32 time samples.       psd: [n/2 + 1] float64 one-sided PSD S_j
+ *   (S_0 may be +inf; S_j for 0 < j < n/2 must be finite and > 0, else RB_ERR_BAD_INPUT,
+ *   detected on the device and reported after the stream synchronises).
+ *   s_hat: [n/2] complex output.            workspace: rb_filter_plan size.
+ */
+int rb_whiten(const rb_filter_desc* desc, const float* strain, const double* psd, float* s_hat,
+              void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rb_basis_filter - steps a2 + a3: basis SNR series and their bin averages.
+ *   beta_k[m] = sum_{j<n/2} s_hat[j] conj(p_k[j]) exp(+2 pi i j m / n)  (Eq. 6-7,
+ *   Sec. III.C third bullet), stored for the valid half m in [n/2, n) only;
+ *   beta_avg_k[i] = (1/w) sum_{r<w} beta_k[i w + r] for valid bins i in [n/(2w), n/w) (Eq. 9).
+ * The multiply by conj(p_k) is fused into the first pass of a four-step inverse Stockham FFT;
+ * the averaging is fused into its last pass.
+ *   s_hat: [n/2] complex (rb_whiten output).  basis->vectors: [k][n/2] complex.
+ *   beta: [k][n/2] complex output (index m - n/2), may be NULL to skip storing it.
+ *   beta_avg: [k][n/(2w)] complex output (index i - n/(2w)).
+ */
+int rb_basis_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* s_hat,
+                    float* beta, float* beta_avg, void* workspace, size_t workspace_bytes,
+                    void* stream);
+
+/*
+ * rb_pack_coeff - lay out the first-stage operand from basis->coeff for desc->precision:
+ *   rows 2t and 2t+1 hold [Re a_t, Im a_t] and [-Im a_t, Re a_t] (k values each, zero
+ *   padded to kp), so that one real GEMM row pair gives Re and Im of sum_k a_tk^* beta_k;
+ *   split precisions store a hi plane then a lo plane (lo = round(x - hi)).
+ *   out: plan.coeff_op_bytes bytes (2 planes x 2T x kp 16-bit values). Enqueue only.
+ *   Errors: RB_ERR_BAD_INPUT for RB_PREC_FP32 (no operand needed) or size mismatch.
+ */
+int rb_pack_coeff(const rb_filter_desc* desc, const rb_basis* basis, void* out, void* stream);
+
+/*
+ * rb_stage1 - step a4: first-stage reconstruction z_avg[t,i] = sum_k conj(a_tk) beta_avg_k[i]
+ * (Eq. 7 applied to Eq. 9) as one contraction over K = 2k, with |z_avg| >= rho_I tested in the
+ * epilogue so the T x bins array never reaches memory (Sec. III.C first stage; Sec. III.E).
+ * RB_PREC_FP32 runs an FP32 SIMT kernel; the 16-bit precisions run a tcgen05 kernel whose
+ * operands TMA loads into shared memory and whose accumulators live in tensor memory.
+ *   beta_avg: [k][n/(2w)] complex (rb_basis_filter output).
+ *   cand: [desc->cand_capacity] output; n_cand (host): number found. Synchronises `stream`.
+ *   Errors: RB_ERR_OVERFLOW when more than cand_capacity candidates exist (*n_cand = count,
+ *   the first cand_capacity found are stored), RB_ERR_BAD_INPUT when coeff_op is missing
+ *   or was packed for another precision.
+ */
+int rb_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* beta_avg,
+              rb_candidate* cand, int64_t* n_cand, void* workspace, size_t workspace_bytes,
+              void* stream);
+
+/*
+ * rb_stage2 - step a5: for each candidate (t, i), z_t[m] = sum_k conj(a_tk) beta_k[m] in FP32
+ * for m in [i w, i w + w); emit the arg-max (ties to the smaller m) when |z| >= rho_II
+ * (Sec. III.C second stage, Sec. III.E custom kernel). One warp per candidate, lanes split k.
+ *   beta: [k][n/2] complex (valid half, rb_basis_filter output).  cand: [n_cand] device.
+ *   trig: [capacity] output; n_trig (host). Synchronises `stream`.
+ *   Errors: RB_ERR_OVERFLOW as for rb_stage1.
+ */
+int rb_stage2(const rb_filter_desc* desc, const rb_basis* basis, const float* beta,
+              const rb_candidate* cand, int64_t n_cand, rb_trigger* trig, int64_t capacity,
+              int64_t* n_trig, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rb_filter - the whole hierarchical filter of one block: a1 (rb_whiten), a2+a3
+ * (rb_basis_filter), a4 (rb_stage1), a5 (rb_stage2), all on `stream`, beta kept in the
+ * workspace. Paper: Sec. III.C (the six bullets) and Sec. III.E.
+ *   strain: [n] float32. psd: [n/2+1] float64.  trig: [capacity]; n_trig (host).
+ *   Errors: as the stage calls; RB_ERR_OVERFLOW from either stage sets *n_trig to the
+ *   required trigger count when known, else to -1 (candidate list overflowed).
+ */
+int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* strain,
+              const double* psd, rb_trigger* trig, int64_t capacity, int64_t* n_trig,
+              void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rb_filter_plain - the template method (Sec. II, Eq. 4; the baseline of Sec. IV.B.2):
+ * per template one inverse FFT of s_hat * conj(h_hat_t), rho = |z| (templates given
+ * unit-normalised), per window of w valid samples the arg-max kept when rho >= rho_II.
+ * The multiply is fused into the FFT's first pass and the window maximum into its last,
+ * so no SNR series reaches memory.
+ *   templates: [T][n/2] complex whitened unit-norm templates (g_t / sigma_t).
+ *   strain, psd, trig, capacity, n_trig: as rb_filter (desc->k, w, rho_ii used; rho_i ignored).
+ */
+int rb_filter_plain(const rb_filter_desc* desc, const float* templates, const float* strain,
+                    const double* psd, rb_trigger* trig, int64_t capacity, int64_t* n_trig,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBMF_H */

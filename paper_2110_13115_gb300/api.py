@@ -1,0 +1,171 @@
+"""Python binding of the C ABI: same names, torch tensors for device memory and streams.
+
+Every function only marshals arguments (device pointers, sizes, the current CUDA
+stream) and calls the shared library; all arithmetic runs in the sm_103a kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+TRIGGER_NP = np.dtype([("sample", np.int64), ("tmpl", np.int32), ("block", np.int32), ("snr", np.float32),
+                       ("phase", np.float32)])
+CANDIDATE_NP = np.dtype([("tmpl", np.int32), ("bin", np.int32), ("snr_avg", np.float32), ("block", np.int32)])
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _lib():
+    return N.load()
+
+
+def make_desc(fs, n, k, n_templates, w=8, precision="fp32", rho_i=0.0, rho_ii=5.0, cand_capacity=1 << 20,
+              sample_offset=0, block_id=0) -> N.rb_filter_desc:
+    prec = N.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return N.rb_filter_desc(float(fs), int(n), int(k), int(n_templates), int(w), prec, float(rho_i), float(rho_ii),
+                            int(cand_capacity), int(sample_offset), int(block_id), 0)
+
+
+def rb_filter_plan(desc) -> N.rb_filter_sizes:
+    out = N.rb_filter_sizes()
+    N.check("rb_filter_plan", _lib().rb_filter_plan(C.byref(desc), C.byref(out)))
+    return out
+
+
+def workspace(desc, device="cuda") -> torch.Tensor:
+    return torch.empty(rb_filter_plan(desc).workspace_bytes, dtype=torch.uint8, device=device)
+
+
+@dataclasses.dataclass
+class Basis:
+    """Device arrays of a reduced basis (see rb_basis in include/rbmf.h)."""
+
+    vectors: torch.Tensor  # complex64 [k][n/2]
+    coeff: torch.Tensor  # complex64 [T][k]
+    n: int
+    coeff_op: torch.Tensor | None = None
+    coeff_op_precision: int = 0
+    sigma2: torch.Tensor | None = None  # float64 [T]
+    singular_values: np.ndarray | None = None
+
+    @property
+    def k(self):
+        return self.vectors.shape[0]
+
+    @property
+    def n_templates(self):
+        return self.coeff.shape[0]
+
+    def c_struct(self) -> N.rb_basis:
+        assert self.vectors.is_contiguous() and self.coeff.is_contiguous()
+        assert self.vectors.dtype == torch.complex64 and self.coeff.dtype == torch.complex64
+        return N.rb_basis(self.k, self.n_templates, int(self.n), self.vectors.data_ptr(), self.coeff.data_ptr(),
+                          self.coeff_op.data_ptr() if self.coeff_op is not None else None,
+                          int(self.coeff_op_precision), 0)
+
+
+def rb_whiten(desc, strain: torch.Tensor, psd: torch.Tensor, ws: torch.Tensor | None = None) -> torch.Tensor:
+    ws = workspace(desc) if ws is None else ws
+    out = torch.empty(desc.n // 2, dtype=torch.complex64, device=strain.device)
+    rc = _lib().rb_whiten(C.byref(desc), _p(strain), _p(psd), _p(out), _p(ws), ws.numel(), _stream())
+    N.check("rb_whiten", rc)
+    return out
+
+
+def rb_basis_filter(desc, basis: Basis, s_hat: torch.Tensor, keep_beta=True, ws=None):
+    ws = workspace(desc) if ws is None else ws
+    dev = s_hat.device
+    half = desc.n // 2
+    nb = rb_filter_plan(desc).n_bins
+    beta = torch.empty((desc.k, half), dtype=torch.complex64, device=dev) if keep_beta else None
+    bavg = torch.empty((desc.k, nb), dtype=torch.complex64, device=dev)
+    b = basis.c_struct()
+    rc = _lib().rb_basis_filter(C.byref(desc), C.byref(b), _p(s_hat), _p(beta), _p(bavg), _p(ws), ws.numel(),
+                                _stream())
+    N.check("rb_basis_filter", rc)
+    return beta, bavg
+
+
+def rb_pack_coeff(desc, basis: Basis) -> Basis:
+    """Pack the first-stage operand for desc.precision into basis.coeff_op (in place)."""
+    sizes = rb_filter_plan(desc)
+    op = torch.empty(sizes.coeff_op_bytes, dtype=torch.uint8, device=basis.coeff.device)
+    b = basis.c_struct()
+    N.check("rb_pack_coeff", _lib().rb_pack_coeff(C.byref(desc), C.byref(b), _p(op), _stream()))
+    basis.coeff_op = op
+    basis.coeff_op_precision = desc.precision
+    return basis
+
+
+def _as_np(buf: torch.Tensor, n: int, dt) -> np.ndarray:
+    raw = buf[: n * dt.itemsize].cpu().numpy()
+    return raw.view(dt).copy()
+
+
+def rb_stage1(desc, basis: Basis, beta_avg: torch.Tensor, ws=None):
+    """Returns (candidates device buffer, count)."""
+    ws = workspace(desc) if ws is None else ws
+    cand = torch.empty(max(desc.cand_capacity, 1) * 16, dtype=torch.uint8, device=beta_avg.device)
+    n = C.c_int64(0)
+    b = basis.c_struct()
+    rc = _lib().rb_stage1(C.byref(desc), C.byref(b), _p(beta_avg), _p(cand), C.byref(n), _p(ws), ws.numel(),
+                          _stream())
+    N.check("rb_stage1", rc)
+    return cand, n.value
+
+
+def rb_stage2(desc, basis: Basis, beta: torch.Tensor, cand: torch.Tensor, n_cand: int, capacity=1 << 20, ws=None):
+    ws = workspace(desc) if ws is None else ws
+    trig = torch.empty(max(capacity, 1) * 24, dtype=torch.uint8, device=beta.device)
+    n = C.c_int64(0)
+    b = basis.c_struct()
+    rc = _lib().rb_stage2(C.byref(desc), C.byref(b), _p(beta), _p(cand), int(n_cand), _p(trig), int(capacity),
+                          C.byref(n), _p(ws), ws.numel(), _stream())
+    N.check("rb_stage2", rc)
+    return trig, n.value
+
+
+def rb_filter(desc, basis: Basis, strain: torch.Tensor, psd: torch.Tensor, capacity=1 << 20, ws=None, trig=None):
+    """Whole hierarchical filter of one block; returns (trigger buffer, count)."""
+    ws = workspace(desc) if ws is None else ws
+    trig = torch.empty(max(capacity, 1) * 24, dtype=torch.uint8, device=strain.device) if trig is None else trig
+    n = C.c_int64(0)
+    b = basis.c_struct()
+    rc = _lib().rb_filter(C.byref(desc), C.byref(b), _p(strain), _p(psd), _p(trig), int(capacity), C.byref(n),
+                          _p(ws), ws.numel(), _stream())
+    N.check("rb_filter", rc)
+    return trig, n.value
+
+
+def rb_filter_plain(desc, templates: torch.Tensor, strain: torch.Tensor, psd: torch.Tensor, capacity=1 << 20,
+                    ws=None, trig=None):
+    """Template-method comparator; templates complex64 [T][n/2] unit-norm whitened."""
+    ws = workspace(desc) if ws is None else ws
+    trig = torch.empty(max(capacity, 1) * 24, dtype=torch.uint8, device=strain.device) if trig is None else trig
+    n = C.c_int64(0)
+    rc = _lib().rb_filter_plain(C.byref(desc), _p(templates), _p(strain), _p(psd), _p(trig), int(capacity),
+                                C.byref(n), _p(ws), ws.numel(), _stream())
+    N.check("rb_filter_plain", rc)
+    return trig, n.value
+
+
+def triggers_numpy(buf: torch.Tensor, n: int) -> np.ndarray:
+    """Device trigger buffer -> numpy structured array sorted by (tmpl, sample)."""
+    a = _as_np(buf, n, TRIGGER_NP)
+    return np.sort(a, order=["tmpl", "sample"])
+
+
+def candidates_numpy(buf: torch.Tensor, n: int) -> np.ndarray:
+    a = _as_np(buf, n, CANDIDATE_NP)
+    return np.sort(a, order=["tmpl", "bin"])

@@ -1,0 +1,383 @@
+// C ABI entry points (include/rbmf.h): validation, workspace carving, orchestration.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+thread_local char g_detail[512] = "";
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Status {
+  unsigned flags;
+  unsigned pad;
+  unsigned long long cand;
+  unsigned long long trig;
+};
+}  // namespace
+
+void rb_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_detail, sizeof(g_detail), "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what,
+           file, line);
+}
+
+namespace rb {
+
+void set_detail(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+  va_end(ap);
+}
+
+int make_geometry(const rb_filter_desc& d, Geometry* g) {
+  if (!(d.fs > 0.0) || !std::isfinite(d.fs)) {
+    set_detail("fs must be finite and > 0");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (!rb_is_pow2(d.n) || d.n < (1 << 10) || d.n > (1 << 20)) {
+    set_detail("n = %lld must be a power of two in [2^10, 2^20]", (long long)d.n);
+    return RB_ERR_BAD_INPUT;
+  }
+  if (d.k < 1 || d.n_templates < 1) {
+    set_detail("k = %d and n_templates = %d must be >= 1", d.k, d.n_templates);
+    return RB_ERR_BAD_INPUT;
+  }
+  if (!(d.w == 1 || d.w == 2 || d.w == 4 || d.w == 8 || d.w == 16)) {
+    set_detail("w = %d must be 1, 2, 4, 8 or 16", d.w);
+    return RB_ERR_BAD_INPUT;
+  }
+  if (!(d.rho_i >= 0.f) || !(d.rho_ii >= 0.f) || !std::isfinite(d.rho_i) || !std::isfinite(d.rho_ii)) {
+    set_detail("thresholds must be finite and >= 0");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (d.cand_capacity < 0 || d.reserved != 0) {
+    set_detail("cand_capacity must be >= 0 and reserved must be 0");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (d.precision < RB_PREC_FP32 || d.precision > RB_PREC_BF16) {
+    set_detail("unknown precision %d", d.precision);
+    return RB_ERR_UNSUPPORTED;
+  }
+  const int p = rb_ilog2(d.n);
+  g->n = d.n;
+  g->n1 = 1 << (p / 2);
+  g->n2 = 1 << (p - p / 2);
+  g->n_bins = d.n / (2 * d.w);
+  g->kp = ((2 * d.k + 63) / 64) * 64;
+  return RB_OK;
+}
+
+size_t coeff_op_bytes(const rb_filter_desc& d, const Geometry& g) {
+  if (d.precision == RB_PREC_FP32) return 0;
+  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
+  return (split ? 2 : 1) * (size_t)2 * d.n_templates * g.kp * 2;
+}
+
+void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws, bool plain) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  char* st = take(256);
+  ws->flags = (unsigned*)st;
+  ws->cand_count = st ? (unsigned long long*)(st + 8) : nullptr;
+  ws->trig_count = st ? (unsigned long long*)(st + 16) : nullptr;
+  ws->host_status = (unsigned long long*)st;
+  const int64_t half = g.n / 2;
+  ws->tables.n1_w = (float2*)take(sizeof(float2) * g.n1);
+  ws->tables.n2_w = (float2*)take(sizeof(float2) * g.n2);
+  ws->tables.fine_w = (float2*)take(sizeof(float2) * g.n2);
+  ws->tables.n1 = ws->tables.n1_w;
+  ws->tables.n2 = ws->tables.n2_w;
+  ws->tables.fine = ws->tables.fine_w;
+  ws->wt = (float*)take(sizeof(float) * half);
+  ws->shat = (float2*)take(sizeof(float2) * half);
+  const int64_t nvec = plain ? d.n_templates : d.k;
+  int64_t vc = (int64_t(32) << 20) / (g.n * 8);
+  vc = std::max<int64_t>(1, std::min<int64_t>(vc, std::min<int64_t>(nvec, 65535)));
+  ws->vc = (int)vc;
+  ws->X = (float2*)take(sizeof(float2) * g.n * vc);
+  if (!plain) {
+    ws->beta = (float2*)take(sizeof(float2) * (size_t)d.k * half);
+    ws->bavg = (float2*)take(sizeof(float2) * (size_t)d.k * g.n_bins);
+    if (d.precision != RB_PREC_FP32) {
+      const size_t plane = (size_t)g.n_bins * g.kp * 2;
+      ws->bop_hi = take(plane);
+      const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
+      ws->bop_lo = split ? take(plane) : nullptr;
+    }
+    ws->cand = (rb_candidate*)take(sizeof(rb_candidate) * (size_t)std::max<int64_t>(d.cand_capacity, 1));
+  }
+  ws->total = off;
+}
+
+}  // namespace rb
+
+using namespace rb;
+
+namespace {
+
+int prepare(const rb_filter_desc* desc, void* workspace, size_t bytes, bool plain, Geometry* g, Workspace* ws,
+            cudaStream_t st) {
+  if (!desc) {
+    set_detail("desc is NULL");
+    return RB_ERR_BAD_INPUT;
+  }
+  int rc = make_geometry(*desc, g);
+  if (rc) return rc;
+  Workspace probe;
+  carve(*desc, *g, nullptr, &probe, plain);
+  if (!workspace || bytes < probe.total || ((uintptr_t)workspace & 255)) {
+    set_detail("workspace %p of %zu bytes; need %zu bytes, 256-byte aligned", workspace, bytes, probe.total);
+    return RB_ERR_OOM;
+  }
+  carve(*desc, *g, (char*)workspace, ws, plain);
+  RB_CUDA_TRY(cudaMemsetAsync(ws->flags, 0, 256, st));
+  return RB_OK;
+}
+
+int read_status(const Workspace& ws, Status* s, cudaStream_t st) {
+  RB_CUDA_TRY(cudaMemcpyAsync(s, ws.host_status, sizeof(Status), cudaMemcpyDeviceToHost, st));
+  RB_CUDA_TRY(cudaStreamSynchronize(st));
+  return RB_OK;
+}
+
+int check_basis(const rb_filter_desc& d, const rb_basis* b) {
+  if (!b || !b->vectors || !b->coeff) {
+    set_detail("basis or its arrays are NULL");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (b->k < d.k || b->n_templates != d.n_templates || b->n != d.n) {
+    set_detail("basis (k=%d, T=%d, n=%lld) does not match desc (k=%d, T=%d, n=%lld)", b->k, b->n_templates,
+               (long long)b->n, d.k, d.n_templates, (long long)d.n);
+    return RB_ERR_BAD_INPUT;
+  }
+  return RB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rb_strerror(int status) {
+  switch (status) {
+    case RB_OK: return "ok";
+    case RB_ERR_BAD_INPUT: return "bad input";
+    case RB_ERR_OOM: return "workspace too small";
+    case RB_ERR_OVERFLOW: return "output overflow";
+    case RB_ERR_TIMEOUT: return "device wait timed out";
+    case RB_ERR_CUDA: return "CUDA error";
+    case RB_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* rb_last_error_detail(void) { return g_detail; }
+
+int rb_version(void) { return 100; }
+
+int rb_filter_plan(const rb_filter_desc* desc, rb_filter_sizes* out) {
+  if (!desc || !out) {
+    set_detail("NULL argument");
+    return RB_ERR_BAD_INPUT;
+  }
+  Geometry g;
+  int rc = make_geometry(*desc, &g);
+  if (rc) return rc;
+  Workspace a, b;
+  carve(*desc, g, nullptr, &a, false);
+  carve(*desc, g, nullptr, &b, true);
+  out->workspace_bytes = std::max(a.total, b.total);
+  out->n_bins = g.n_bins;
+  out->n1 = g.n1;
+  out->n2 = g.n2;
+  out->kp = g.kp;
+  out->coeff_op_bytes = coeff_op_bytes(*desc, g);
+  return RB_OK;
+}
+
+int rb_whiten(const rb_filter_desc* desc, const float* strain, const double* psd, float* s_hat, void* workspace,
+              size_t workspace_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Geometry g;
+  Workspace ws;
+  int rc = prepare(desc, workspace, workspace_bytes, true, &g, &ws, st);
+  if (rc) return rc;
+  if (!strain || !psd || !s_hat) {
+    set_detail("NULL array");
+    return RB_ERR_BAD_INPUT;
+  }
+  if ((rc = init_tables(g, ws, psd, desc->fs, st))) return rc;
+  if ((rc = whiten(g, ws, strain, (float2*)s_hat, st))) return rc;
+  Status s;
+  if ((rc = read_status(ws, &s, st))) return rc;
+  if (s.flags & RB_FLAG_BAD_PSD) {
+    set_detail("PSD not finite and positive on 0 < j < n/2");
+    return RB_ERR_BAD_INPUT;
+  }
+  return RB_OK;
+}
+
+int rb_basis_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* s_hat, float* beta,
+                    float* beta_avg, void* workspace, size_t workspace_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Geometry g;
+  Workspace ws;
+  int rc = prepare(desc, workspace, workspace_bytes, false, &g, &ws, st);
+  if (rc) return rc;
+  if ((rc = check_basis(*desc, basis))) return rc;
+  if (!s_hat || !beta_avg) {
+    set_detail("NULL array");
+    return RB_ERR_BAD_INPUT;
+  }
+  if ((rc = init_tables(g, ws, nullptr, desc->fs, st))) return rc;
+  return bank_filter(g, ws, (const float2*)basis->vectors, desc->k, (const float2*)s_hat, (float2*)beta,
+                     (float2*)beta_avg, desc->w, st);
+}
+
+int rb_pack_coeff(const rb_filter_desc* desc, const rb_basis* basis, void* out, void* stream) {
+  if (!desc) return RB_ERR_BAD_INPUT;
+  Geometry g;
+  int rc = make_geometry(*desc, &g);
+  if (rc) return rc;
+  if ((rc = check_basis(*desc, basis))) return rc;
+  if (desc->precision == RB_PREC_FP32 || !out) {
+    set_detail("no packed operand for FP32 (or out is NULL)");
+    return RB_ERR_BAD_INPUT;
+  }
+  return pack_coeff(*desc, *basis, g, out, (cudaStream_t)stream);
+}
+
+static int run_stage1(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
+                      const float2* bavg, rb_candidate* cand, cudaStream_t st) {
+  if (d.precision == RB_PREC_FP32) return stage1_simt(d, b, g, ws, bavg, cand, st);
+  if (!b.coeff_op || b.coeff_op_precision != d.precision) {
+    set_detail("coeff_op missing or packed for precision %d (need %d)", b.coeff_op_precision, d.precision);
+    return RB_ERR_BAD_INPUT;
+  }
+  int rc = pack_beta(d, g, bavg, ws.bop_hi, ws.bop_lo, st);
+  if (rc) return rc;
+  return stage1_tc(d, b, g, ws, cand, st);
+}
+
+int rb_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* beta_avg, rb_candidate* cand,
+              int64_t* n_cand, void* workspace, size_t workspace_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Geometry g;
+  Workspace ws;
+  int rc = prepare(desc, workspace, workspace_bytes, false, &g, &ws, st);
+  if (rc) return rc;
+  if ((rc = check_basis(*desc, basis))) return rc;
+  if (!beta_avg || !cand || !n_cand) {
+    set_detail("NULL array");
+    return RB_ERR_BAD_INPUT;
+  }
+  if ((rc = run_stage1(*desc, *basis, g, ws, (const float2*)beta_avg, cand, st))) return rc;
+  Status s;
+  if ((rc = read_status(ws, &s, st))) return rc;
+  *n_cand = (int64_t)s.cand;
+  return (int64_t)s.cand > desc->cand_capacity ? RB_ERR_OVERFLOW : RB_OK;
+}
+
+int rb_stage2(const rb_filter_desc* desc, const rb_basis* basis, const float* beta, const rb_candidate* cand,
+              int64_t n_cand, rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* workspace,
+              size_t workspace_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Geometry g;
+  Workspace ws;
+  int rc = prepare(desc, workspace, workspace_bytes, false, &g, &ws, st);
+  if (rc) return rc;
+  if ((rc = check_basis(*desc, basis))) return rc;
+  if (!beta || (n_cand > 0 && !cand) || !n_trig || capacity < 0 || n_cand < 0 || (capacity > 0 && !trig)) {
+    set_detail("NULL array or negative count");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (n_cand > 0 &&
+      (rc = stage2(*desc, *basis, (const float2*)beta, cand, nullptr, n_cand, trig, capacity, ws.trig_count, st)))
+    return rc;
+  Status s;
+  if ((rc = read_status(ws, &s, st))) return rc;
+  *n_trig = (int64_t)s.trig;
+  return (int64_t)s.trig > capacity ? RB_ERR_OVERFLOW : RB_OK;
+}
+
+int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* strain, const double* psd,
+              rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* workspace, size_t workspace_bytes,
+              void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Geometry g;
+  Workspace ws;
+  int rc = prepare(desc, workspace, workspace_bytes, false, &g, &ws, st);
+  if (rc) return rc;
+  if ((rc = check_basis(*desc, basis))) return rc;
+  if (!strain || !psd || !n_trig || capacity < 0 || (capacity > 0 && !trig)) {
+    set_detail("NULL array or negative capacity");
+    return RB_ERR_BAD_INPUT;
+  }
+  if ((rc = init_tables(g, ws, psd, desc->fs, st))) return rc;
+  if ((rc = whiten(g, ws, strain, ws.shat, st))) return rc;
+  if ((rc = bank_filter(g, ws, (const float2*)basis->vectors, desc->k, ws.shat, ws.beta, ws.bavg, desc->w, st)))
+    return rc;
+  if ((rc = run_stage1(*desc, *basis, g, ws, ws.bavg, ws.cand, st))) return rc;
+  if ((rc = stage2(*desc, *basis, ws.beta, ws.cand, ws.cand_count, 0, trig, capacity, ws.trig_count, st)))
+    return rc;
+  Status s;
+  if ((rc = read_status(ws, &s, st))) return rc;
+  if (s.flags & RB_FLAG_BAD_PSD) {
+    set_detail("PSD not finite and positive on 0 < j < n/2");
+    return RB_ERR_BAD_INPUT;
+  }
+  if ((int64_t)s.cand > desc->cand_capacity) {
+    *n_trig = -1;
+    set_detail("%llu first-stage candidates exceed cand_capacity %lld", s.cand, (long long)desc->cand_capacity);
+    return RB_ERR_OVERFLOW;
+  }
+  *n_trig = (int64_t)s.trig;
+  if ((int64_t)s.trig > capacity) {
+    set_detail("%llu triggers exceed capacity %lld", s.trig, (long long)capacity);
+    return RB_ERR_OVERFLOW;
+  }
+  return RB_OK;
+}
+
+int rb_filter_plain(const rb_filter_desc* desc, const float* templates, const float* strain, const double* psd,
+                    rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* workspace, size_t workspace_bytes,
+                    void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Geometry g;
+  Workspace ws;
+  int rc = prepare(desc, workspace, workspace_bytes, true, &g, &ws, st);
+  if (rc) return rc;
+  if (!templates || !strain || !psd || !n_trig || capacity < 0 || (capacity > 0 && !trig)) {
+    set_detail("NULL array or negative capacity");
+    return RB_ERR_BAD_INPUT;
+  }
+  if ((rc = init_tables(g, ws, psd, desc->fs, st))) return rc;
+  if ((rc = whiten(g, ws, strain, ws.shat, st))) return rc;
+  if ((rc = plain_filter(g, ws, (const float2*)templates, desc->n_templates, ws.shat, desc->w,
+                         desc->rho_ii * desc->rho_ii, desc->sample_offset, desc->block_id, trig, capacity, st)))
+    return rc;
+  Status s;
+  if ((rc = read_status(ws, &s, st))) return rc;
+  if (s.flags & RB_FLAG_BAD_PSD) {
+    set_detail("PSD not finite and positive on 0 < j < n/2");
+    return RB_ERR_BAD_INPUT;
+  }
+  *n_trig = (int64_t)s.trig;
+  if ((int64_t)s.trig > capacity) {
+    set_detail("%llu triggers exceed capacity %lld", s.trig, (long long)capacity);
+    return RB_ERR_OVERFLOW;
+  }
+  return RB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,661 @@
+// Hot path of the hierarchical reduced-basis matched filter (arXiv:2110.13115, Sec. III.C/E):
+//   a1 whitening forward FFT, a2+a3 basis SNR series with bin averages, the template-method
+//   comparator, the FP32 first stage, operand packing for the tensor-core first stage, and
+//   the second stage. Host entry points of the C ABI (include/rbmf.h) are at the bottom.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "fft.cuh"
+#include "internal.h"
+
+using namespace rbfft;
+
+namespace {
+
+enum { MODE_BANK = 0, MODE_STRAIN = 1, MODE_PLAIN = 2 };
+
+// ---------------------------------------------------------------------------------------
+// Set-up: twiddle tables (FP64 sincospi rounded to FP32) and the whitening weights
+//   wt[j] = dt * sqrt(4 df / S_j) for 0 < j < n/2 (0 at DC).
+// tables: tab_n1[n1] = exp(2 pi i e/n1), tab_n2[n2] = exp(2 pi i e/n2), tab_fine[n2] = exp(2 pi i e/n)
+__global__ void k_init(float2* tab_n1, float2* tab_n2, float2* tab_fine, int n1, int n2, float* wt,
+                       const double* psd, int64_t half, double dt, double df, unsigned* flags) {
+  const int64_t n = (int64_t)n1 * n2;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = tid; e < n1 + 2 * n2; e += stride) {
+    double s, c;
+    if (e < n1) {
+      sincospi(2.0 * (double)e / n1, &s, &c);
+      tab_n1[e] = make_float2((float)c, (float)s);
+    } else if (e < n1 + n2) {
+      const int64_t i = e - n1;
+      sincospi(2.0 * (double)i / n2, &s, &c);
+      tab_n2[i] = make_float2((float)c, (float)s);
+    } else {
+      const int64_t i = e - n1 - n2;
+      sincospi(2.0 * (double)i / (double)n, &s, &c);
+      tab_fine[i] = make_float2((float)c, (float)s);
+    }
+  }
+  if (wt == nullptr) return;
+  for (int64_t j = tid; j < half; j += stride) {
+    if (j == 0) {
+      wt[0] = 0.f;
+      continue;
+    }
+    const double S = psd[j];
+    if (!(S > 0.0) || isinf(S) || isnan(S)) {
+      atomicOr(flags, (unsigned)RB_FLAG_BAD_PSD);
+      wt[j] = 0.f;
+    } else {
+      wt[j] = (float)(dt * sqrt(4.0 * df / S));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Pass A of the four-step transform: G columns j1 of length L = n2.
+//  MODE_BANK : x[j] = s_hat[j] * conj(rows[vec][j]) for j < n/2 (zero above: the one-sided
+//              filter of Eq. 1), inverse sign. rows = basis vectors or unit-norm templates.
+//  MODE_STRAIN: x[j] = strain[j], forward sign.
+// Output X[vec][j1][m2] (m2 fastest) = w_n^(j1 m2) * inner transform.
+template <int MODE, int L, int G>
+__global__ void __launch_bounds__(G * L / kE) k_pass_a(const float2* __restrict__ rows,
+                                                       const float2* __restrict__ shat,
+                                                       const float* __restrict__ strain,
+                                                       float2* __restrict__ X,
+                                                       const float2* __restrict__ tab_n2,
+                                                       const float2* __restrict__ tab_n1,
+                                                       const float2* __restrict__ tab_fine, int n1,
+                                                       int64_t vec0) {
+  constexpr int SIGN = MODE == MODE_STRAIN ? -1 : 1;
+  constexpr int LOG2L = __builtin_ctz(L);
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* sdata = smem + L;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < L; e += blockDim.x) tw[e] = tab_n2[e];
+  __syncthreads();
+  const int c = tid % G, tj = tid / G;
+  const int j1 = blockIdx.x * G + c;
+  const int64_t half = (int64_t)n1 * L / 2;
+  const float2* row = rows + (vec0 + blockIdx.y) * half;
+  float2 v[kE];
+  auto load = [&](int j2) -> float2 {
+    const int64_t j = (int64_t)j1 + (int64_t)n1 * j2;
+    if constexpr (MODE == MODE_STRAIN) {
+      return make_float2(__ldg(strain + j), 0.f);
+    } else {
+      if (j2 >= L / 2) return make_float2(0.f, 0.f);
+      return cmulc(__ldg(shat + j), __ldcs(row + j));
+    }
+  };
+  column_transform<SIGN, L, G>(v, c, tj, sdata, tw, load);
+  __syncthreads();
+  constexpr int RL = LastPass<L>::R;
+#pragma unroll
+  for (int b = 0; b < kE / RL; ++b)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int m2 = final_point<L>(tj, b, r);
+      const int rr = j1 * m2;  // < n
+      float2 t = cmul(__ldg(tab_n1 + (rr >> LOG2L)), __ldg(tab_fine + (rr & (L - 1))));
+      if (SIGN < 0) t.y = -t.y;
+      sdata[c * (L + 1) + m2] = cmul(v[b * RL + r], t);
+    }
+  __syncthreads();
+  float2* xo = X + ((int64_t)blockIdx.y * n1 + (int64_t)blockIdx.x * G) * L;
+  for (int idx = tid; idx < G * L; idx += blockDim.x) {
+    const int cc = idx >> LOG2L, m2 = idx & (L - 1);
+    xo[idx] = sdata[cc * (L + 1) + m2];
+  }
+}
+
+template <int L, int G>
+constexpr int pass_a_smem_bytes() {
+  return (L + std::max(Smem<L, G>::data, G * (L + 1))) * 8;
+}
+
+// ---------------------------------------------------------------------------------------
+// Pass B: 16 columns m2 of length L = n1, input X[vec][j1][m2]; output sample
+// m = m2 + n2 m1 of the long transform.
+//  MODE_BANK  : keep m in [n/2, n): beta[vec][m - n/2] and the W-sample bin means
+//               beta_avg[vec][(m - n/2)/W] (Eq. 9).
+//  MODE_STRAIN: keep m in [0, n/2): s_hat[m] = wt[m] * Y[m] (whitening, Sec. III.E).
+//  MODE_PLAIN : keep m in [n/2, n): rho^2 = |Y|^2, window arg-max over W samples,
+//               trigger when rho^2 >= thr2 (template method, Eq. 4).
+struct PassBArgs {
+  const float2* X;
+  int n2;
+  int64_t vec0;
+  float2* beta;
+  float2* beta_avg;
+  float2* shat;
+  const float* wt;
+  rb_trigger* trig;
+  unsigned long long* counter;
+  int64_t cap;
+  float thr2;
+  int64_t sample_offset;
+  int block_id;
+};
+
+template <int MODE, int L, int W>
+__global__ void __launch_bounds__(L) k_pass_b(PassBArgs a, const float2* __restrict__ tab_n1) {
+  constexpr int G = 16;
+  constexpr int SIGN = MODE == MODE_STRAIN ? -1 : 1;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* sdata = smem + L;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < L; e += blockDim.x) tw[e] = tab_n1[e];
+  __syncthreads();
+  const int c = tid % G, tj = tid / G;
+  const int n2 = a.n2;
+  const int m2 = blockIdx.x * G + c;
+  const float2* xin = a.X + (int64_t)blockIdx.y * L * n2;
+  float2 v[kE];
+  auto load = [&](int j1) -> float2 { return xin[(int64_t)j1 * n2 + m2]; };
+  column_transform<SIGN, L, G>(v, c, tj, sdata, tw, load);
+  const int64_t n = (int64_t)L * n2, half = n / 2;
+  const int64_t vec = a.vec0 + blockIdx.y;
+  constexpr int RL = LastPass<L>::R;
+#pragma unroll
+  for (int b = 0; b < kE / RL; ++b)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int m1 = final_point<L>(tj, b, r);
+      const int64_t m = m2 + (int64_t)n2 * m1;
+      const float2 val = v[b * RL + r];
+      if constexpr (MODE == MODE_STRAIN) {
+        if (m1 < L / 2) a.shat[m] = cscale(val, __ldg(a.wt + m));
+      } else if constexpr (MODE == MODE_BANK) {
+        float2 s = val;
+#pragma unroll
+        for (int off = 1; off < W; off <<= 1) {
+          s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+          s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+        }
+        if (m1 >= L / 2) {
+          if (a.beta) __stcs(a.beta + vec * half + (m - half), val);
+          if ((c & (W - 1)) == 0)
+            a.beta_avg[vec * (half / W) + (m - half) / W] = cscale(s, 1.0f / W);
+        }
+      } else {
+        float r2 = cabs2(val);
+        int64_t mb = m;
+        float2 vb = val;
+#pragma unroll
+        for (int off = 1; off < W; off <<= 1) {
+          const float r2o = __shfl_xor_sync(0xffffffffu, r2, off);
+          const int64_t mo = __shfl_xor_sync(0xffffffffu, mb, off);
+          const float vx = __shfl_xor_sync(0xffffffffu, vb.x, off);
+          const float vy = __shfl_xor_sync(0xffffffffu, vb.y, off);
+          if (r2o > r2 || (r2o == r2 && mo < mb)) {
+            r2 = r2o;
+            mb = mo;
+            vb = make_float2(vx, vy);
+          }
+        }
+        if (m1 >= L / 2 && (c & (W - 1)) == 0 && r2 >= a.thr2) {
+          const unsigned long long idx = atomicAdd(a.counter, 1ull);
+          if ((int64_t)idx < a.cap) {
+            rb_trigger t;
+            t.sample = a.sample_offset + mb;
+            t.tmpl = (int32_t)vec;
+            t.block = a.block_id;
+            t.snr = sqrtf(r2);
+            t.phase = atan2f(vb.y, vb.x);
+            a.trig[idx] = t;
+          }
+        }
+      }
+    }
+}
+
+template <int L>
+constexpr int pass_b_smem_bytes() {
+  return (L + Smem<L, 16>::data) * 8;
+}
+
+// ---------------------------------------------------------------------------------------
+// First stage in FP32 (SIMT): z_avg[t, i] = sum_k conj(a_tk) beta_avg_k[i] over a 64x64 tile,
+// |z_avg|^2 >= thr2 tested in registers, candidates appended (Sec. III.C first stage).
+__global__ void __launch_bounds__(256) k_stage1_simt(const float2* __restrict__ coeff, int ldk,
+                                                     const float2* __restrict__ bavg, int T, int k,
+                                                     int nb, float thr2, int bin0, int block_id,
+                                                     rb_candidate* cand, unsigned long long* counter,
+                                                     int64_t cap) {
+  __shared__ float2 As[16][65];
+  __shared__ float2 Bs[16][64];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int t0 = blockIdx.y * 64, i0 = blockIdx.x * 64;
+  float2 acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < k; k0 += 16) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = tid + 256 * e;
+      const int tt = idx >> 4, kk = idx & 15;
+      As[kk][tt] = (t0 + tt < T && k0 + kk < k) ? coeff[(int64_t)(t0 + tt) * ldk + k0 + kk] : make_float2(0.f, 0.f);
+      const int kb = idx >> 6, ii = idx & 63;
+      Bs[kb][ii] = (k0 + kb < k && i0 + ii < nb) ? bavg[(int64_t)(k0 + kb) * nb + i0 + ii] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float2 av[4], bv[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) av[p] = As[kk][ty + 16 * p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[p][q].x = fmaf(av[p].x, bv[q].x, fmaf(av[p].y, bv[q].y, acc[p][q].x));
+          acc[p][q].y = fmaf(av[p].x, bv[q].y, fmaf(-av[p].y, bv[q].x, acc[p][q].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = t0 + ty + 16 * p, i = i0 + tx + 16 * q;
+      if (t < T && i < nb) {
+        const float r2 = cabs2(acc[p][q]);
+        if (r2 >= thr2) {
+          const unsigned long long idx = atomicAdd(counter, 1ull);
+          if ((int64_t)idx < cap) {
+            rb_candidate cd;
+            cd.tmpl = t;
+            cd.bin = bin0 + i;
+            cd.snr_avg = sqrtf(r2);
+            cd.block = block_id;
+            cand[idx] = cd;
+          }
+        }
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Second stage (Sec. III.C): one warp per candidate, lanes split the basis index k; the W
+// full-rate samples of the bin are reduced across the warp; arg-max (first on ties).
+template <int W>
+__global__ void __launch_bounds__(256) k_stage2(const float2* __restrict__ coeff, int ldk,
+                                                const float2* __restrict__ beta, int k, int T, int64_t half,
+                                                const rb_candidate* __restrict__ cand,
+                                                const unsigned long long* dev_count, int64_t cand_cap,
+                                                int64_t host_count, float thr2, int64_t sample_offset,
+                                                rb_trigger* trig, unsigned long long* counter,
+                                                int64_t cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int64_t ncand = host_count;
+  if (dev_count) ncand = (int64_t)min((unsigned long long)cand_cap, *dev_count);
+  for (int64_t ci = gw; ci < ncand; ci += nw) {
+    const rb_candidate cd = cand[ci];
+    // caller-provided candidates: skip anything outside the valid bins or the bank
+    if (cd.tmpl < 0 || cd.tmpl >= T || (int64_t)cd.bin * W < half || (int64_t)cd.bin * W >= 2 * half) continue;
+    const int64_t mb = (int64_t)cd.bin * W - half;
+    float2 acc[W];
+#pragma unroll
+    for (int r = 0; r < W; ++r) acc[r] = make_float2(0.f, 0.f);
+    const float2* arow = coeff + (int64_t)cd.tmpl * ldk;
+    for (int kk = lane; kk < k; kk += 32) {
+      const float2 av = __ldg(arow + kk);
+      const float2* bp = beta + (int64_t)kk * half + mb;
+#pragma unroll
+      for (int r = 0; r < W; ++r) {
+        const float2 bv = __ldg(bp + r);
+        acc[r].x = fmaf(av.x, bv.x, fmaf(av.y, bv.y, acc[r].x));
+        acc[r].y = fmaf(av.x, bv.y, fmaf(-av.y, bv.x, acc[r].y));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < W; ++r)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, off);
+        acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, off);
+      }
+    if (lane == 0) {
+      int best = 0;
+      float r2b = cabs2(acc[0]);
+      float2 zb = acc[0];
+#pragma unroll
+      for (int r = 1; r < W; ++r) {
+        const float r2 = cabs2(acc[r]);
+        if (r2 > r2b) {
+          r2b = r2;
+          best = r;
+          zb = acc[r];
+        }
+      }
+      if (r2b >= thr2) {
+        const unsigned long long idx = atomicAdd(counter, 1ull);
+        if ((int64_t)idx < cap) {
+          rb_trigger t;
+          t.sample = sample_offset + (int64_t)cd.bin * W + best;
+          t.tmpl = cd.tmpl;
+          t.block = cd.block;
+          t.snr = sqrtf(r2b);
+          t.phase = atan2f(zb.y, zb.x);
+          trig[idx] = t;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Operand packing for the tensor-core first stage (16-bit planes, hi then lo).
+template <typename T16>
+__device__ __forceinline__ T16 to16(float x);
+template <>
+__device__ __forceinline__ __half to16<__half>(float x) { return __float2half_rn(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ float from16(__half x) { return __half2float(x); }
+__device__ __forceinline__ float from16(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// rows 2t: [Re a_t(0..k), Im a_t(0..k), 0..]; rows 2t+1: [-Im a_t, Re a_t, 0..]
+template <typename T16>
+__global__ void k_pack_coeff(const float2* __restrict__ coeff, int ldk, int T, int k, int kp,
+                             T16* __restrict__ hi, T16* __restrict__ lo) {
+  const int64_t total = (int64_t)2 * T * kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / kp;
+    const int col = (int)(idx - row * kp);
+    const int64_t t = row >> 1;
+    const bool im = row & 1;
+    float x = 0.f;
+    if (col < k) {
+      const float2 a = coeff[t * ldk + col];
+      x = im ? -a.y : a.x;
+    } else if (col < 2 * k) {
+      const float2 a = coeff[t * ldk + col - k];
+      x = im ? a.x : a.y;
+    }
+    const T16 h = to16<T16>(x);
+    hi[idx] = h;
+    if (lo) lo[idx] = to16<T16>(x - from16(h));
+  }
+}
+
+// beta_avg [k][nb] complex -> [nb][kp] rows: [Re beta_avg(:, i), Im beta_avg(:, i), 0..]
+template <typename T16>
+__global__ void __launch_bounds__(256) k_pack_beta(const float2* __restrict__ bavg, int k, int nb, int kp,
+                                                   T16* __restrict__ hi, T16* __restrict__ lo) {
+  __shared__ float2 tile[32][33];
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 32
+  for (int r = ty; r < 32; r += 8) {
+    const int kk = k0 + r, ii = i0 + tx;
+    tile[r][tx] = (kk < k && ii < nb) ? bavg[(int64_t)kk * nb + ii] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int ii = i0 + r, kk = k0 + tx;
+    if (ii >= nb) continue;
+    const float2 b = tile[tx][r];
+    const int64_t base = (int64_t)ii * kp;
+    if (kk < k) {
+      const T16 hr = to16<T16>(b.x), hm = to16<T16>(b.y);
+      hi[base + kk] = hr;
+      hi[base + k + kk] = hm;
+      if (lo) {
+        lo[base + kk] = to16<T16>(b.x - from16(hr));
+        lo[base + k + kk] = to16<T16>(b.y - from16(hm));
+      }
+    }
+    // zero padding columns [2k, kp) once per row (block column 0 only)
+    if (blockIdx.y == 0) {
+      for (int col = 2 * k + tx; col < kp; col += 32) {
+        hi[base + col] = to16<T16>(0.f);
+        if (lo) lo[base + col] = to16<T16>(0.f);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Launch helpers (template dispatch on the column length)
+
+template <typename K>
+static cudaError_t allow_smem(K kernel, int bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int L>
+struct GA {
+  static constexpr int value = L >= 512 ? 8 : (L >= 128 ? 16 : 32);
+};
+
+template <int MODE, int L>
+static int launch_a_L(const rb::Geometry& g, const float2* rows, const float2* shat, const float* strain,
+                      float2* X, const rb::Tables& tb, int64_t vec0, int nvec, cudaStream_t st) {
+  constexpr int G = GA<L>::value;
+  constexpr int smem = pass_a_smem_bytes<L, G>();
+  auto kern = k_pass_a<MODE, L, G>;
+  RB_CUDA_TRY(allow_smem(kern, smem));
+  dim3 grid(g.n1 / G, nvec);
+  kern<<<grid, G * L / kE, smem, st>>>(rows, shat, strain, X, tb.n2, tb.n1, tb.fine, g.n1, vec0);
+  RB_LAUNCH_CHECK();
+  return RB_OK;
+}
+
+template <int MODE>
+static int launch_a(const rb::Geometry& g, const float2* rows, const float2* shat, const float* strain,
+                    float2* X, const rb::Tables& tb, int64_t vec0, int nvec, cudaStream_t st) {
+  switch (g.n2) {
+    case 32: return launch_a_L<MODE, 32>(g, rows, shat, strain, X, tb, vec0, nvec, st);
+    case 64: return launch_a_L<MODE, 64>(g, rows, shat, strain, X, tb, vec0, nvec, st);
+    case 128: return launch_a_L<MODE, 128>(g, rows, shat, strain, X, tb, vec0, nvec, st);
+    case 256: return launch_a_L<MODE, 256>(g, rows, shat, strain, X, tb, vec0, nvec, st);
+    case 512: return launch_a_L<MODE, 512>(g, rows, shat, strain, X, tb, vec0, nvec, st);
+    case 1024: return launch_a_L<MODE, 1024>(g, rows, shat, strain, X, tb, vec0, nvec, st);
+  }
+  rb::set_detail("unsupported inner FFT length %d", g.n2);
+  return RB_ERR_UNSUPPORTED;
+}
+
+template <int MODE, int L, int W>
+static int launch_b_LW(const rb::Geometry& g, const PassBArgs& a, const rb::Tables& tb, int nvec,
+                       cudaStream_t st) {
+  constexpr int smem = pass_b_smem_bytes<L>();
+  auto kern = k_pass_b<MODE, L, W>;
+  RB_CUDA_TRY(allow_smem(kern, smem));
+  dim3 grid(g.n2 / 16, nvec);
+  kern<<<grid, L, smem, st>>>(a, tb.n1);
+  RB_LAUNCH_CHECK();
+  return RB_OK;
+}
+
+template <int MODE, int L>
+static int launch_b_L(const rb::Geometry& g, const PassBArgs& a, const rb::Tables& tb, int nvec, int w,
+                      cudaStream_t st) {
+  if constexpr (MODE == MODE_STRAIN) return launch_b_LW<MODE, L, 1>(g, a, tb, nvec, st);
+  switch (w) {
+    case 1: return launch_b_LW<MODE, L, 1>(g, a, tb, nvec, st);
+    case 2: return launch_b_LW<MODE, L, 2>(g, a, tb, nvec, st);
+    case 4: return launch_b_LW<MODE, L, 4>(g, a, tb, nvec, st);
+    case 8: return launch_b_LW<MODE, L, 8>(g, a, tb, nvec, st);
+    case 16: return launch_b_LW<MODE, L, 16>(g, a, tb, nvec, st);
+  }
+  rb::set_detail("unsupported bin width %d", w);
+  return RB_ERR_BAD_INPUT;
+}
+
+template <int MODE>
+static int launch_b(const rb::Geometry& g, const PassBArgs& a, const rb::Tables& tb, int nvec, int w,
+                    cudaStream_t st) {
+  switch (g.n1) {
+    case 32: return launch_b_L<MODE, 32>(g, a, tb, nvec, w, st);
+    case 64: return launch_b_L<MODE, 64>(g, a, tb, nvec, w, st);
+    case 128: return launch_b_L<MODE, 128>(g, a, tb, nvec, w, st);
+    case 256: return launch_b_L<MODE, 256>(g, a, tb, nvec, w, st);
+    case 512: return launch_b_L<MODE, 512>(g, a, tb, nvec, w, st);
+    case 1024: return launch_b_L<MODE, 1024>(g, a, tb, nvec, w, st);
+  }
+  rb::set_detail("unsupported outer FFT length %d", g.n1);
+  return RB_ERR_UNSUPPORTED;
+}
+
+template <int W>
+static int launch_stage2_W(const rb_filter_desc& d, const rb_basis& b, const float2* beta,
+                           const rb_candidate* cand, const unsigned long long* dev_count,
+                           int64_t host_count, rb_trigger* trig, int64_t cap,
+                           unsigned long long* counter, cudaStream_t st) {
+  const int64_t half = d.n / 2;
+  const int threads = 256;
+  int64_t blocks = dev_count ? 152 * 8 : std::max<int64_t>(1, (host_count + 7) / 8);
+  blocks = std::min<int64_t>(blocks, 152 * 64);
+  k_stage2<W><<<(unsigned)blocks, threads, 0, st>>>(
+      reinterpret_cast<const float2*>(b.coeff), b.k, beta, d.k, d.n_templates, half, cand, dev_count,
+      d.cand_capacity, host_count, d.rho_ii * d.rho_ii, d.sample_offset, trig, counter, cap);
+  RB_LAUNCH_CHECK();
+  return RB_OK;
+}
+
+}  // namespace
+
+// =======================================================================================
+// Host orchestration (namespace rb, used by the C ABI below and by other translation units)
+
+namespace rb {
+
+int init_tables(const Geometry& g, const Workspace& ws, const double* psd, double fs, cudaStream_t st) {
+  const double dt = 1.0 / fs, df = fs / (double)g.n;
+  const int64_t work = std::max<int64_t>(g.n1 + 2 * g.n2, psd ? g.n / 2 : 0);
+  const int blocks = (int)std::min<int64_t>(1024, (work + 255) / 256);
+  k_init<<<blocks, 256, 0, st>>>(ws.tables.n1_w, ws.tables.n2_w, ws.tables.fine_w, g.n1, g.n2,
+                                 psd ? ws.wt : nullptr, psd, g.n / 2, dt, df, ws.flags);
+  RB_LAUNCH_CHECK();
+  return RB_OK;
+}
+
+int whiten(const Geometry& g, const Workspace& ws, const float* strain, float2* shat, cudaStream_t st) {
+  int rc = launch_a<MODE_STRAIN>(g, nullptr, nullptr, strain, ws.X, ws.tables, 0, 1, st);
+  if (rc) return rc;
+  PassBArgs a{};
+  a.X = ws.X;
+  a.n2 = g.n2;
+  a.shat = shat;
+  a.wt = ws.wt;
+  return launch_b<MODE_STRAIN>(g, a, ws.tables, 1, 1, st);
+}
+
+int bank_filter(const Geometry& g, const Workspace& ws, const float2* rows, int64_t nvec, const float2* shat,
+                float2* beta, float2* bavg, int w, cudaStream_t st) {
+  for (int64_t v0 = 0; v0 < nvec; v0 += ws.vc) {
+    const int cnt = (int)std::min<int64_t>(ws.vc, nvec - v0);
+    int rc = launch_a<MODE_BANK>(g, rows, shat, nullptr, ws.X, ws.tables, v0, cnt, st);
+    if (rc) return rc;
+    PassBArgs a{};
+    a.X = ws.X;
+    a.n2 = g.n2;
+    a.vec0 = v0;
+    a.beta = beta;
+    a.beta_avg = bavg;
+    rc = launch_b<MODE_BANK>(g, a, ws.tables, cnt, w, st);
+    if (rc) return rc;
+  }
+  return RB_OK;
+}
+
+int plain_filter(const Geometry& g, const Workspace& ws, const float2* tmpl, int64_t T, const float2* shat,
+                 int w, float thr2, int64_t sample_offset, int block_id, rb_trigger* trig, int64_t cap,
+                 cudaStream_t st) {
+  for (int64_t v0 = 0; v0 < T; v0 += ws.vc) {
+    const int cnt = (int)std::min<int64_t>(ws.vc, T - v0);
+    int rc = launch_a<MODE_BANK>(g, tmpl, shat, nullptr, ws.X, ws.tables, v0, cnt, st);
+    if (rc) return rc;
+    PassBArgs a{};
+    a.X = ws.X;
+    a.n2 = g.n2;
+    a.vec0 = v0;
+    a.trig = trig;
+    a.counter = ws.trig_count;
+    a.cap = cap;
+    a.thr2 = thr2;
+    a.sample_offset = sample_offset;
+    a.block_id = block_id;
+    rc = launch_b<MODE_PLAIN>(g, a, ws.tables, cnt, w, st);
+    if (rc) return rc;
+  }
+  return RB_OK;
+}
+
+int stage1_simt(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
+                const float2* bavg, rb_candidate* cand, cudaStream_t st) {
+  const int nb = (int)g.n_bins;
+  dim3 grid((nb + 63) / 64, (d.n_templates + 63) / 64);
+  k_stage1_simt<<<grid, 256, 0, st>>>(reinterpret_cast<const float2*>(b.coeff), b.k, bavg, d.n_templates,
+                                      d.k, nb, d.rho_i * d.rho_i, nb, d.block_id, cand, ws.cand_count,
+                                      d.cand_capacity);
+  RB_LAUNCH_CHECK();
+  return RB_OK;
+}
+
+int pack_beta(const rb_filter_desc& d, const Geometry& g, const float2* bavg, void* hi, void* lo,
+              cudaStream_t st) {
+  const int nb = (int)g.n_bins;
+  dim3 grid((nb + 31) / 32, (d.k + 31) / 32);
+  const bool bf = d.precision == RB_PREC_BF16 || d.precision == RB_PREC_BF16_SPLIT;
+  if (bf)
+    k_pack_beta<__nv_bfloat16><<<grid, 256, 0, st>>>(bavg, d.k, nb, g.kp, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo);
+  else
+    k_pack_beta<__half><<<grid, 256, 0, st>>>(bavg, d.k, nb, g.kp, (__half*)hi, (__half*)lo);
+  RB_LAUNCH_CHECK();
+  return RB_OK;
+}
+
+int stage2(const rb_filter_desc& d, const rb_basis& b, const float2* beta, const rb_candidate* cand,
+           const unsigned long long* dev_count, int64_t host_count, rb_trigger* trig, int64_t cap,
+           unsigned long long* counter, cudaStream_t st) {
+  switch (d.w) {
+    case 1: return launch_stage2_W<1>(d, b, beta, cand, dev_count, host_count, trig, cap, counter, st);
+    case 2: return launch_stage2_W<2>(d, b, beta, cand, dev_count, host_count, trig, cap, counter, st);
+    case 4: return launch_stage2_W<4>(d, b, beta, cand, dev_count, host_count, trig, cap, counter, st);
+    case 8: return launch_stage2_W<8>(d, b, beta, cand, dev_count, host_count, trig, cap, counter, st);
+    case 16: return launch_stage2_W<16>(d, b, beta, cand, dev_count, host_count, trig, cap, counter, st);
+  }
+  return RB_ERR_BAD_INPUT;
+}
+
+int pack_coeff(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, void* out, cudaStream_t st) {
+  const int64_t plane = (int64_t)2 * d.n_templates * g.kp;
+  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
+  const bool bf = d.precision == RB_PREC_BF16 || d.precision == RB_PREC_BF16_SPLIT;
+  const int blocks = (int)std::min<int64_t>(4096, (plane + 255) / 256);
+  if (bf) {
+    auto* h = (__nv_bfloat16*)out;
+    k_pack_coeff<__nv_bfloat16><<<blocks, 256, 0, st>>>(reinterpret_cast<const float2*>(b.coeff), b.k,
+                                                        d.n_templates, d.k, g.kp, h, split ? h + plane : nullptr);
+  } else {
+    auto* h = (__half*)out;
+    k_pack_coeff<__half><<<blocks, 256, 0, st>>>(reinterpret_cast<const float2*>(b.coeff), b.k,
+                                                 d.n_templates, d.k, g.kp, h, split ? h + plane : nullptr);
+  }
+  RB_LAUNCH_CHECK();
+  return RB_OK;
+}
+
+}  // namespace rb

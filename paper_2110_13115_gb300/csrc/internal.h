@@ -1,0 +1,71 @@
+// Internal host-side interfaces shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+#include "../../include/rbmf.h"
+
+namespace rb {
+
+struct Geometry {
+  int64_t n = 0;       // block length
+  int n1 = 0, n2 = 0;  // four-step split n = n1 * n2 (outer x inner)
+  int64_t n_bins = 0;  // valid bins n / (2 w)
+  int kp = 0;          // 2k rounded up to 64 (first-stage contraction length)
+};
+
+struct Tables {
+  float2* n1_w = nullptr;    // [n1] exp(2 pi i e / n1)
+  float2* n2_w = nullptr;    // [n2] exp(2 pi i e / n2)
+  float2* fine_w = nullptr;  // [n2] exp(2 pi i e / n)
+  const float2* n1 = nullptr;
+  const float2* n2 = nullptr;
+  const float2* fine = nullptr;
+};
+
+// Carving of the caller's workspace (all offsets 256-byte aligned).
+struct Workspace {
+  unsigned* flags = nullptr;                 // RB_FLAG_* bits
+  unsigned long long* cand_count = nullptr;  // first-stage candidates found
+  unsigned long long* trig_count = nullptr;  // triggers found
+  unsigned long long* host_status = nullptr; // (device) copy-out block: flags, counts
+  Tables tables;
+  float* wt = nullptr;        // [n/2] whitening weights
+  float2* shat = nullptr;     // [n/2] whitened data
+  float2* X = nullptr;        // [vc][n1][n2] four-step intermediate
+  int vc = 1;                 // vectors per four-step chunk
+  float2* beta = nullptr;     // [k][n/2]
+  float2* bavg = nullptr;     // [k][n_bins]
+  void* bop_hi = nullptr;     // [n_bins][kp] 16-bit
+  void* bop_lo = nullptr;     // [n_bins][kp] 16-bit (split precisions)
+  rb_candidate* cand = nullptr;
+  size_t total = 0;
+};
+
+void set_detail(const char* fmt, ...);
+int make_geometry(const rb_filter_desc& d, Geometry* g);
+// base == nullptr: only compute the size (ws->total)
+void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws, bool plain);
+size_t coeff_op_bytes(const rb_filter_desc& d, const Geometry& g);
+
+int init_tables(const Geometry& g, const Workspace& ws, const double* psd, double fs, cudaStream_t st);
+int whiten(const Geometry& g, const Workspace& ws, const float* strain, float2* shat, cudaStream_t st);
+int bank_filter(const Geometry& g, const Workspace& ws, const float2* rows, int64_t nvec, const float2* shat,
+                float2* beta, float2* bavg, int w, cudaStream_t st);
+int plain_filter(const Geometry& g, const Workspace& ws, const float2* tmpl, int64_t T, const float2* shat,
+                 int w, float thr2, int64_t sample_offset, int block_id, rb_trigger* trig, int64_t cap,
+                 cudaStream_t st);
+int stage1_simt(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
+                const float2* bavg, rb_candidate* cand, cudaStream_t st);
+int pack_beta(const rb_filter_desc& d, const Geometry& g, const float2* bavg, void* hi, void* lo,
+              cudaStream_t st);
+int pack_coeff(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, void* out, cudaStream_t st);
+int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
+              rb_candidate* cand, cudaStream_t st);
+int stage2(const rb_filter_desc& d, const rb_basis& b, const float2* beta, const rb_candidate* cand,
+           const unsigned long long* dev_count, int64_t host_count, rb_trigger* trig, int64_t cap,
+           unsigned long long* counter, cudaStream_t st);
+
+}  // namespace rb

@@ -108,6 +108,19 @@ def white_draws(nf: int, seed: int) -> np.ndarray:
     return xy[0] + 1j * xy[1]
 
 
+def complex_normal(shape, seed: int) -> np.ndarray:
+    """Standard complex normal draws (E|x|^2 = 2) of the given shape, complex128."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(size=shape) + 1j * rng.standard_normal(size=shape)
+
+
+def unit_rows(rows: int, cols: int, seed: int) -> np.ndarray:
+    """Rows of complex normal draws scaled to unit Euclidean norm, column 0 zero (DC)."""
+    x = complex_normal((rows, cols), seed)
+    x[:, 0] = 0.0
+    return x / np.linalg.norm(x, axis=1, keepdims=True)
+
+
 def coloured_noise(grid: Grid, psd: np.ndarray, seed: int, scale: float = 1.0) -> np.ndarray:
     """Gaussian noise with one-sided PSD ``scale * psd`` as a float64 time series.
 

@@ -1,0 +1,220 @@
+"""GPU parity of the filter path (a1-a5, template method) against the FP64 oracle.
+
+Both sides consume the same seeded inputs; the CUDA path is reached only through the C ABI
+(paper_2110_13115_gb300.api -> librbmf.so).
+"""
+import numpy as np
+import pytest
+
+from oracle import mf, rb
+from paper_2110_13115_gb300 import inputs
+
+from parity_util import BAND, compare_triggers
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_13115_gb300 import api as A, _native as N
+
+    N.load()
+    return A
+
+
+def _strain(n, fs=1024.0, seed=0, inj=None):
+    inj = n >= (1 << 13) if inj is None else inj
+    g = inputs.Grid(fs=fs, n=n, f_low=30.0)
+    psd = inputs.analytic_psd(g)
+    x = inputs.coloured_noise(g, psd, inputs.noise_seed(seed, 0))
+    if inj:
+        spec = inputs.BankSpec(1, 10.0, 30.0, 0.0, 2)
+        for j in inputs.draw_injections(spec, g, 1, 12.0, seed=7 + seed):
+            x = x + inputs.injection_series(g, psd, j, 2)
+    return g, psd, x.astype(np.float32)
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+@pytest.mark.parametrize("n", [1 << 10, 1 << 11, 1 << 13, 1 << 14, 1 << 16, 1 << 19])
+def test_whiten_parity(api, n):
+    g, psd, x = _strain(n, fs=2048.0 if n >= (1 << 16) else 1024.0)
+    d = api.make_desc(g.fs, n, 1, 1, w=1)
+    sh = api.rb_whiten(d, _dev(x), _dev(psd)).cpu().numpy()
+    ref = rb.whitened_data(mf.strain_fd(x.astype(np.float64), g.fs), psd, n, g.fs)
+    err = np.abs(sh - ref).max() / np.sqrt(np.mean(np.abs(ref) ** 2))
+    assert err < 2e-5, err
+    assert sh[0] == 0
+
+
+@pytest.mark.parametrize("n,k,w", [(1 << 12, 8, 1), (1 << 13, 24, 4), (1 << 14, 24, 8), (1 << 17, 16, 16),
+                                   (1 << 15, 40, 2)])
+def test_basis_filter_parity(api, n, k, w):
+    g, psd, x = _strain(n)
+    half = n // 2
+    P = inputs.unit_rows(k, half, seed=100 + k)
+    d = api.make_desc(g.fs, n, k, 1, w=w)
+    basis = api.Basis(_dev(P, torch.complex64), _dev(np.ones((1, k)), torch.complex64), n)
+    sh = api.rb_whiten(d, _dev(x), _dev(psd))
+    beta, bavg = api.rb_basis_filter(d, basis, sh)
+    beta, bavg = beta.cpu().numpy(), bavg.cpu().numpy()
+    s_fd = mf.strain_fd(x.astype(np.float64), g.fs)
+    ref = rb.basis_series(s_fd, psd, P.astype(np.complex64).astype(np.complex128), n, g.fs)
+    rref = ref[:, half:]
+    scale = np.sqrt(np.mean(np.abs(rref) ** 2))
+    assert np.abs(beta - rref).max() / scale < 3e-5
+    aref = rb.bin_average(ref, w)[:, n // (2 * w):]
+    assert np.abs(bavg - aref).max() / scale < 3e-5
+
+
+def test_basis_filter_full_size_sampled_rows(api):
+    """n = 2^19, k = 256 in the benchmark's launch configuration; 4 rows checked one by one."""
+    n, k, w = 1 << 19, 256, 8
+    g, psd, x = _strain(n, fs=2048.0)
+    half = n // 2
+    P = inputs.unit_rows(k, half, seed=5).astype(np.complex64)
+    d = api.make_desc(g.fs, n, k, 1, w=w)
+    basis = api.Basis(_dev(P), _dev(np.ones((1, k), np.complex64)), n)
+    sh = api.rb_whiten(d, _dev(x), _dev(psd))
+    beta, bavg = api.rb_basis_filter(d, basis, sh)
+    s_fd = mf.strain_fd(x.astype(np.float64), g.fs)
+    for row in [0, 77, 200, 255]:
+        ref = rb.basis_series(s_fd, psd, P[row:row + 1].astype(np.complex128), n, g.fs)
+        rref = ref[0, half:]
+        got = beta[row].cpu().numpy()
+        scale = np.sqrt(np.mean(np.abs(rref) ** 2))
+        assert np.abs(got - rref).max() / scale < 5e-5, row
+        aref = rb.bin_average(ref, w)[0, n // (2 * w):]
+        assert np.abs(bavg[row].cpu().numpy() - aref).max() / scale < 5e-5, row
+
+
+def _rand_coeff(T, k, seed):
+    a = inputs.complex_normal((T, k), seed)
+    return a / np.linalg.norm(a, axis=1, keepdims=True)
+
+
+@pytest.mark.parametrize("T,k,w,rho_i", [(200, 24, 8, 3.0), (130, 16, 1, 3.3), (64, 40, 16, 2.6)])
+def test_stage1_fp32_parity(api, T, k, w, rho_i):
+    n = 1 << 14
+    nb = n // (2 * w)
+    a = _rand_coeff(T, k, 1).astype(np.complex64)
+    bv = inputs.complex_normal((k, nb), 2).astype(np.complex64)
+    d = api.make_desc(1024.0, n, k, T, w=w, rho_i=rho_i, cand_capacity=1 << 16)
+    basis = api.Basis(_dev(np.zeros((k, n // 2), np.complex64)), _dev(a), n)
+    buf, nc = api.rb_stage1(d, basis, _dev(bv))
+    got = api.candidates_numpy(buf, nc)
+    full = np.zeros((k, n // w), np.complex128)
+    full[:, nb:] = bv
+    ref, r = rb.stage1(a.astype(np.complex128), full, n, w, rho_i)
+    gset = set(zip(got["tmpl"].tolist(), got["bin"].tolist()))
+    oset = set(zip(ref["template"].tolist(), ref["bin"].tolist()))
+    for t, i in gset ^ oset:
+        assert abs(r[t, i - nb] - rho_i) <= BAND * rho_i, (t, i)
+    assert len(oset) > 20
+    m = {(int(c["tmpl"]), int(c["bin"])): float(c["snr_avg"]) for c in got}
+    for c in ref:
+        key = (int(c["template"]), int(c["bin"]))
+        if key in m:
+            assert abs(m[key] - c["snr_avg"]) <= 1e-5 * c["snr_avg"]
+
+
+@pytest.mark.parametrize("w", [1, 2, 4, 8, 16])
+def test_stage2_parity(api, w):
+    n, k, T = 1 << 14, 24, 50
+    half = n // 2
+    a = _rand_coeff(T, k, 3).astype(np.complex64)
+    beta = inputs.complex_normal((k, half), 4).astype(np.complex64)
+    rng = np.random.default_rng(5)
+    nb = n // (2 * w)
+    cands = np.zeros(400, dtype=api.CANDIDATE_NP)
+    cands["tmpl"] = rng.integers(0, T, 400)
+    cands["bin"] = nb + rng.integers(0, nb, 400)
+    cands = np.unique(cands)
+    d = api.make_desc(1024.0, n, k, T, w=w, rho_ii=2.2)
+    basis = api.Basis(_dev(np.zeros((k, half), np.complex64)), _dev(a), n)
+    cbuf = _dev(cands.view(np.uint8))
+    buf, nt = api.rb_stage2(d, basis, _dev(beta), cbuf, len(cands))
+    got = api.triggers_numpy(buf, nt)
+    full = np.zeros((k, n), np.complex128)
+    full[:, half:] = beta
+    oc = np.zeros(len(cands), dtype=rb.CAND_DTYPE)
+    oc["template"] = cands["tmpl"]
+    oc["bin"] = cands["bin"]
+    ref = rb.stage2(a.astype(np.complex128), full, oc, w, 2.2)
+    zr = np.abs(np.conj(a.astype(np.complex128)) @ beta.astype(np.complex128))
+    stats = compare_triggers(got, ref, w, 2.2, ref_rho=zr)
+    assert stats["both"] > 50
+
+
+@pytest.mark.parametrize("n,k,T,w", [(1 << 14, 24, 40, 8), (1 << 13, 16, 33, 4), (1 << 12, 8, 17, 16),
+                                     (1 << 14, 12, 20, 1)])
+def test_filter_end_to_end_fp32(api, n, k, T, w):
+    g, psd, x = _strain(n, seed=1)
+    half = n // 2
+    P = inputs.unit_rows(k, half, seed=11).astype(np.complex64)
+    a = _rand_coeff(T, k, 12).astype(np.complex64)
+    # random white rows decorrelate neighbouring samples, so the bin mean shrinks as 1/sqrt(w)
+    rho_i, rho_ii = 2.2 / np.sqrt(w), 3.0
+    d = api.make_desc(g.fs, n, k, T, w=w, rho_i=rho_i, rho_ii=rho_ii, cand_capacity=1 << 18)
+    basis = api.Basis(_dev(P), _dev(a), n)
+    buf, nt = api.rb_filter(d, basis, _dev(x), _dev(psd))
+    got = api.triggers_numpy(buf, nt)
+    s_fd = mf.strain_fd(x.astype(np.float64), g.fs)
+    P64, a64 = P.astype(np.complex128), a.astype(np.complex128)
+    ref, cands, beta = rb.hierarchical_triggers(a64, s_fd, psd, P64, n, g.fs, w, rho_i, rho_ii)
+    zfull = np.abs(rb.reconstruct(a64, beta[:, half:]))
+    ravg = np.abs(rb.reconstruct(a64, rb.bin_average(beta, w)[:, n // (2 * w):]))
+    stats = compare_triggers(got, ref, w, rho_ii, ref_rho=zfull, rho_avg=ravg, rho_i=rho_i)
+    assert stats["both"] >= 5, stats
+
+
+@pytest.mark.parametrize("n,T,w", [(1 << 14, 48, 8), (1 << 12, 20, 1), (1 << 16, 8, 16)])
+def test_filter_plain_parity(api, n, T, w):
+    g, psd, x = _strain(n, seed=2)
+    half = n // 2
+    rows = inputs.unit_rows(T, half, seed=21).astype(np.complex64)
+    rho_ii = 3.2
+    d = api.make_desc(g.fs, n, 1, T, w=w, rho_ii=rho_ii)
+    buf, nt = api.rb_filter_plain(d, _dev(rows), _dev(x), _dev(psd))
+    got = api.triggers_numpy(buf, nt)
+    s_fd = mf.strain_fd(x.astype(np.float64), g.fs)
+    z = rb.basis_series(s_fd, psd, rows.astype(np.complex128), n, g.fs)
+    rho = np.abs(z)
+    ref = np.concatenate([mf.window_triggers(t, rho[t], z[t], n, w, rho_ii) for t in range(T)])
+    stats = compare_triggers(got, ref, w, rho_ii, ref_rho=rho[:, half:])
+    assert stats["both"] > 10, stats
+
+
+def test_overflow_and_errors(api):
+    from paper_2110_13115_gb300 import _native as N
+
+    n, T = 1 << 12, 8
+    g, psd, x = _strain(n, seed=3)
+    rows = inputs.unit_rows(T, n // 2, seed=31).astype(np.complex64)
+    d = api.make_desc(g.fs, n, 1, T, w=1, rho_ii=0.5)
+    _, full = api.rb_filter_plain(d, _dev(rows), _dev(x), _dev(psd))
+    assert full > 100
+    with pytest.raises(N.RBError) as e:
+        api.rb_filter_plain(d, _dev(rows), _dev(x), _dev(psd), capacity=10)
+    assert e.value.code == N.RB_ERR_OVERFLOW
+    # no triggers at an unreachable threshold
+    d2 = api.make_desc(g.fs, n, 1, T, w=1, rho_ii=1e6)
+    assert api.rb_filter_plain(d2, _dev(rows), _dev(x), _dev(psd))[1] == 0
+    # a negative PSD bin is rejected
+    bad = psd.copy()
+    bad[100] = -1.0
+    with pytest.raises(N.RBError) as e:
+        api.rb_whiten(d, _dev(x), _dev(bad))
+    assert e.value.code == N.RB_ERR_BAD_INPUT
+    # too small a workspace
+    with pytest.raises(N.RBError) as e:
+        api.rb_whiten(d, _dev(x), _dev(psd), ws=torch.empty(1024, dtype=torch.uint8, device="cuda"))
+    assert e.value.code == N.RB_ERR_OOM
