@@ -212,6 +212,58 @@ int rb_filter_plain(const rb_filter_desc* desc, const float* templates, const fl
                     const double* psd, rb_trigger* trig, int64_t capacity, int64_t* n_trig,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/* A bank of closed-form stationary-phase chirps h(f) = f^(-7/6) exp(-i Psi(f)) (the
+ * synthetic stand-in for the paper's IMRPhenomPv2 bank, Sec. III.B), with
+ * Psi = -pi/4 + 3/(128 eta v^5) [1 + (20/9)(743/336 + 11 eta/4) v^2 + (4 beta - 16 pi) v^3],
+ * v = (pi M f)^(1/3), supported on f_low <= f < 1/(6^(3/2) pi M), 0 < j < n/2. */
+typedef struct rb_bank_desc {
+  double fs;              /* sample rate [Hz] */
+  int64_t n;              /* block length (as rb_filter_desc.n) */
+  double f_low;           /* lower cutoff [Hz] */
+  int32_t n_templates;    /* T */
+  int32_t pn_order;       /* 0: Newtonian; 2: through 1PN; 3: adds the 1.5PN tail and spin-orbit */
+  const double* params;   /* HOST [T][4]: m1, m2 [solar masses], chi1, chi2 (aligned spins) */
+} rb_bank_desc;
+
+/*
+ * rb_build_plan - workspace sizes for rb_templates and rb_build (host only).
+ *   oversample: extra sketch columns beyond k (randomised range finder); l = min(k + oversample, T).
+ * Errors: RB_ERR_BAD_INPUT (sizes, n, pn_order, k > T).
+ */
+int rb_build_plan(const rb_bank_desc* bank, int32_t k, int32_t oversample, size_t* templates_bytes /* host */,
+                  size_t* build_bytes /* host */);
+
+/*
+ * rb_templates - whitened, unit-normalised templates g_t / sigma_t on j in [0, n/2) (rows of the
+ * template matrix of Sec. III.B: "whitened ... and normalized to unity"), with
+ * g_t[j] = sqrt(4 df / S_j) h_t(f_j) and sigma_t^2 = sum_j |g_t[j]|^2 = <h_t|h_t> (Eq. 2) in FP64.
+ * The phase is evaluated in FP64, reduced modulo 2 pi, then sin/cos in FP32.
+ *   psd: [n/2+1] float64 device.  out: [T][n/2] complex device.  sigma2: [T] float64 device.
+ *   workspace: templates_bytes of rb_build_plan. Enqueue only.
+ */
+int rb_templates(const rb_bank_desc* bank, const double* psd, float* out, double* sigma2, void* workspace,
+                 size_t workspace_bytes, void* stream);
+
+/*
+ * rb_build - step a0: the reduced basis of a bank (Sec. III.A-B; Eq. 5b; Eq. 7 coefficients).
+ * The unit-normalised whitened template matrix G (T x n/2, rows from rb_templates) is decomposed
+ * by a randomised subspace iteration: Y = G^H Omega (Omega T x l seeded complex normal), then
+ * `power_iters` rounds of Y <- G^H (G Q^H) with Q the orthonormalised Y; orthonormalisation is
+ * CholeskyQR2 with FP64 Gram matrices; a Rayleigh-Ritz step (FP64 eigen-decomposition of the
+ * l x l matrix B^H B, B = G Q^H, on the host) gives the singular values and the basis
+ * p_k = sum_i conj(V[i][k]) q_i. Sketch products run in FP32 with FP64 accumulation across
+ * K-slices. Outputs (all caller-owned):
+ *   vectors: [k][n/2] complex device, orthonormal rows (the basis P of Eq. 5b).
+ *   coeff:   [T][k] complex device, a_tk = <g_t/sigma_t | p_k> (normalised coefficients).
+ *   sigma2:  [T] float64 device (exact FP64 template norms).
+ *   sv:      [k] float64 HOST, leading singular values of G, descending.
+ * Synchronises `stream`. Errors: RB_ERR_BAD_INPUT (k < 1, k > T, bad PSD), RB_ERR_OOM
+ * (workspace smaller than build_bytes), RB_ERR_UNSUPPORTED (l > 1024).
+ */
+int rb_build(const rb_bank_desc* bank, const double* psd, int32_t k, int32_t oversample, int32_t power_iters,
+             uint64_t seed, float* vectors, float* coeff, double* sigma2, double* sv, void* workspace,
+             size_t workspace_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,13 @@ class rb_filter_sizes(C.Structure):
                 ("kp", C.c_int32), ("coeff_op_bytes", C.c_size_t)]
 
 
+class rb_bank_desc(C.Structure):
+    _fields_ = [("fs", C.c_double), ("n", C.c_int64), ("f_low", C.c_double), ("n_templates", C.c_int32),
+                ("pn_order", C.c_int32), ("params", C.c_void_p)]
+
+
+EXTRA_STRUCTS = {"rb_bank_desc": rb_bank_desc}
+
 assert C.sizeof(rb_trigger) == 24 and C.sizeof(rb_candidate) == 16
 
 _P = C.c_void_p
@@ -75,6 +82,17 @@ SIGNATURES = {
     "rb_stage2": (C.c_int, [_D, _B, _P, _P, C.c_int64, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_plain": (C.c_int, [_D, _P, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
+    "rb_build_plan": (C.c_int, [C.POINTER(rb_bank_desc), C.c_int32, C.c_int32, C.POINTER(C.c_size_t),
+                                C.POINTER(C.c_size_t)]),
+    "rb_templates": (C.c_int, [C.POINTER(rb_bank_desc), _P, _P, _P, _P, C.c_size_t, _P]),
+    "rb_build": (C.c_int, [C.POINTER(rb_bank_desc), _P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _P, _P, _P,
+                           C.POINTER(C.c_double), _P, C.c_size_t, _P]),
+}
+
+# host-only helpers exported for the CPU tests of the FP64 linear algebra (not in the header)
+HOST_HOOKS = {
+    "rbx_herm_eig": (C.c_int, [C.c_int, _P, _P, _P]),
+    "rbx_cholesky": (C.c_int, [C.c_int, _P, _P]),
 }
 
 _lib = None
@@ -94,7 +112,7 @@ def load(path: str = LIB_PATH):
     if not os.path.exists(path):
         raise ImportError(f"{path} is not built: run `python -m paper_2110_13115_gb300.build`")
     lib = C.CDLL(path)
-    for name, (res, args) in SIGNATURES.items():
+    for name, (res, args) in list(SIGNATURES.items()) + list(HOST_HOOKS.items()):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args

@@ -169,3 +169,55 @@ def triggers_numpy(buf: torch.Tensor, n: int) -> np.ndarray:
 def candidates_numpy(buf: torch.Tensor, n: int) -> np.ndarray:
     a = _as_np(buf, n, CANDIDATE_NP)
     return np.sort(a, order=["tmpl", "bin"])
+
+
+# --- bank and basis construction ----------------------------------------------------------
+
+class Bank:
+    """Host-side bank description (parameters stay on the host, as the C ABI states)."""
+
+    def __init__(self, params: np.ndarray, fs: float, n: int, f_low: float, pn_order: int):
+        self.params = np.ascontiguousarray(params, dtype=np.float64)
+        assert self.params.ndim == 2 and self.params.shape[1] == 4
+        self.fs, self.n, self.f_low, self.pn_order = float(fs), int(n), float(f_low), int(pn_order)
+
+    def c_struct(self) -> N.rb_bank_desc:
+        return N.rb_bank_desc(self.fs, self.n, self.f_low, self.params.shape[0], self.pn_order,
+                              self.params.ctypes.data)
+
+
+def rb_build_plan(bank: Bank, k: int, oversample: int = 64):
+    t = C.c_size_t(0)
+    b = C.c_size_t(0)
+    bd = bank.c_struct()
+    N.check("rb_build_plan", _lib().rb_build_plan(C.byref(bd), int(k), int(oversample), C.byref(t), C.byref(b)))
+    return t.value, b.value
+
+
+def rb_templates(bank: Bank, psd: torch.Tensor):
+    """Whitened unit-norm templates [T][n/2] complex64 and sigma^2 [T] float64 (device)."""
+    tb, _ = rb_build_plan(bank, 1, 0)
+    ws = torch.empty(tb, dtype=torch.uint8, device=psd.device)
+    T = bank.params.shape[0]
+    out = torch.empty((T, bank.n // 2), dtype=torch.complex64, device=psd.device)
+    s2 = torch.empty(T, dtype=torch.float64, device=psd.device)
+    bd = bank.c_struct()
+    N.check("rb_templates", _lib().rb_templates(C.byref(bd), _p(psd), _p(out), _p(s2), _p(ws), ws.numel(), _stream()))
+    return out, s2
+
+
+def rb_build(bank: Bank, psd: torch.Tensor, k: int, oversample: int = 64, power_iters: int = 1, seed: int = 12345):
+    """Reduced basis of the bank (step a0); returns a Basis with sigma2 and singular values."""
+    _, bb = rb_build_plan(bank, k, oversample)
+    ws = torch.empty(bb, dtype=torch.uint8, device=psd.device)
+    T = bank.params.shape[0]
+    vec = torch.empty((k, bank.n // 2), dtype=torch.complex64, device=psd.device)
+    coeff = torch.empty((T, k), dtype=torch.complex64, device=psd.device)
+    s2 = torch.empty(T, dtype=torch.float64, device=psd.device)
+    sv = (C.c_double * k)()
+    bd = bank.c_struct()
+    rc = _lib().rb_build(C.byref(bd), _p(psd), int(k), int(oversample), int(power_iters), C.c_uint64(seed), _p(vec),
+                         _p(coeff), _p(s2), sv, _p(ws), ws.numel(), _stream())
+    N.check("rb_build", rc)
+    del ws
+    return Basis(vec, coeff, bank.n, sigma2=s2, singular_values=np.array(sv[:]))

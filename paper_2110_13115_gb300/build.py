@@ -38,12 +38,22 @@ def _compile(src: str, obj: str, extra) -> str:
     return r.stderr
 
 
+def _compile_cpp(src: str, obj: str, extra) -> str:
+    cmd = [shutil.which("g++") or "g++", "-O2", "-std=c++17", "-fPIC", "-I", os.path.join(ROOT, "include"),
+           "-c", src, "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"g++ failed for {src}:\n{r.stdout}\n{r.stderr}")
+    return r.stderr
+
+
 def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu"))) + sorted(glob.glob(os.path.join(CSRC, "*.cpp")))
+    objs = [os.path.join(OUT_DIR, os.path.splitext(os.path.basename(s))[0] + ".o") for s in srcs]
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        logs = list(ex.map(lambda so: _compile(so[0], so[1], list(extra)), zip(srcs, objs)))
+        logs = list(ex.map(lambda so: (_compile_cpp if so[0].endswith(".cpp") else _compile)(so[0], so[1], list(extra)),
+                           zip(srcs, objs)))
     if verbose:
         for s, lg in zip(srcs, logs):
             if lg.strip():
