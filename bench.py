@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Throughput of the hierarchical reduced-basis matched filter on one block per GPU.
+
+One step = one pass of the whole hot path over one 256 s block at 2048 Hz (n = 2^19) against a
+10,000-template bank (masses 3-50, aligned spins, 1.5PN stationary-phase chirps) with a k = 256
+basis: whitening FFT, basis filter + bin average, first-stage reconstruction with fused threshold,
+second-stage recomputation (rb_filter). Metric: template-seconds filtered per second, counting the
+n/2 unique valid seconds of a block (arXiv:2110.13115 Sec. IV.B.2 throughput, Sec. III.F blocks).
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU FP64 oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "template-seconds filtered/sec (RB hierarchical vs full FFT MF) at <=1e-3 SNR loss"
+UNIT = "template-seconds/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp16_split")
+    p.add_argument("--w", type=int, default=8)
+    p.add_argument("--k", type=int, default=256)
+    p.add_argument("--templates", type=int, default=10000)
+    p.add_argument("--n", type=int, default=524288)
+    p.add_argument("--recovery", type=float, default=0.99)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle timing (the template method of the FP64 oracle, one process per core, spawn)
+
+_W = {}
+
+
+def _oracle_init(strain, psd, fs, n, f_low, pn, w, rho_ii, bank):
+    from oracle import mf
+
+    _W.update(s_fd=mf.strain_fd(strain.astype(np.float64), fs), psd=psd, fs=fs, n=n, f_low=f_low, pn=pn, w=w,
+              rho_ii=rho_ii, bank=bank)
+
+
+def _oracle_one(t):
+    from oracle import mf, waveform
+
+    h = waveform.template(_W["bank"][t], _W["fs"], _W["n"], _W["f_low"], _W["pn"])
+    z, sig = mf.snr_series(_W["s_fd"], h, _W["psd"], _W["n"], _W["fs"])
+    return len(mf.window_triggers(t, np.abs(z) / sig, z, _W["n"], _W["w"], _W["rho_ii"]))
+
+
+def oracle_rate(wl, seconds_budget, pool=None, cores=None):
+    """Template-seconds/s of the oracle's template method on a bounded sample of the bank."""
+    cores = cores or len(os.sched_getaffinity(0))
+    own = pool is None
+    if own:
+        ctx = mp.get_context("spawn")
+        g = wl.grid
+        pool = ctx.Pool(cores, initializer=_oracle_init,
+                        initargs=(wl.strain, wl.psd, g.fs, g.n, g.f_low, wl.bank_spec.pn_order, wl.w, wl.rho_ii,
+                                  wl.bank))
+    try:
+        # one warm-up template per worker, then as many templates as fit the budget
+        pool.map(_oracle_one, range(cores))
+        t0 = time.perf_counter()
+        done = 0
+        T = len(wl.bank)
+        batch = cores * 2
+        while time.perf_counter() - t0 < seconds_budget:
+            idx = [(done + i) % T for i in range(batch)]
+            pool.map(_oracle_one, idx)
+            done += batch
+        wall = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    secs = wl.grid.n // 2 / wl.grid.fs
+    return done * secs / wall, done, wall, cores
+
+
+def run_reference(args):
+    from paper_2110_13115_gb300 import inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = inputs.full(w=args.w, k=args.k, n_templates=args.templates, n=args.n)
+    cores = len(os.sched_getaffinity(0))
+    ctx = mp.get_context("spawn")
+    g = wl.grid
+    pool = ctx.Pool(cores, initializer=_oracle_init,
+                    initargs=(wl.strain, wl.psd, g.fs, g.n, g.f_low, wl.bank_spec.pn_order, wl.w, wl.rho_ii, wl.bank))
+    per_step = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
+    rates = []
+    with pool:
+        for i in range(args.warmup + args.steps):
+            r, done, wall, _ = oracle_rate(wl, per_step, pool=pool, cores=cores)
+            if i >= args.warmup:
+                rates.append((r, done, wall))
+    value = len(rates) and sum(d for _, d, _ in rates) * (g.n // 2 / g.fs) / sum(w for _, _, w in rates)
+    ms = 1e3 * sum(w for _, _, w in rates) / max(len(rates), 1)
+    out = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+               ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+               data="synthetic", impl="reference",
+               config=dict(workload=wl.name, templates=len(wl.bank), block_samples=g.n, fs=g.fs, w=args.w),
+               cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle",
+                                 sample=f"template method (FP64 numpy FFT per template) on a bounded sample of "
+                                        f"{sum(d for _, d, _ in rates)} template filterings over {args.steps} steps"),
+               e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------------------------------
+# clocks during the timed region
+
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = f"/tmp/rb_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        if not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+
+
+# ----------------------------------------------------------------------------------------
+
+def source_hash(*paths):
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel_key, src_hash):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path)).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+    if not d or d.get("source_hash") != src_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def calibrate_rho_i(api, basis, templates, psd_d, wl_cal, args, torch):
+    """Largest rho_I with n_final >= recovery * n_flat at rho_II on a noise-only block (Eq. 16):
+    the (1 - recovery) quantile of the bin-averaged SNR over the bins of the flat triggers."""
+    g = wl_cal.grid
+    T = len(wl_cal.bank)
+    strain = torch.from_numpy(wl_cal.strain).cuda()
+    dp = api.make_desc(g.fs, g.n, args.k, T, w=args.w, rho_ii=wl_cal.rho_ii)
+    buf, nflat = api.rb_filter_plain(dp, templates, strain, psd_d, capacity=1 << 22)
+    flat = api.triggers_numpy(buf, nflat)
+    if nflat == 0:
+        return 3.0, 0
+    probe = 3.0
+    while True:
+        d = api.make_desc(g.fs, g.n, args.k, T, w=args.w, precision="fp32", rho_i=probe, cand_capacity=1 << 26)
+        ws = api.workspace(d)
+        sh = api.rb_whiten(d, strain, psd_d, ws=ws)
+        _, bavg = api.rb_basis_filter(d, basis, sh, keep_beta=False, ws=ws)
+        cand, nc = api.rb_stage1(d, basis, bavg, ws=ws)
+        cands = api.candidates_numpy(cand, nc)
+        del ws, cand, bavg
+        look = {(int(c["tmpl"]), int(c["bin"])): float(c["snr_avg"]) for c in cands}
+        vals = np.array([look.get((int(t["tmpl"]), int(t["sample"]) // args.w), 0.0) for t in flat])
+        # bins below the probe threshold are unknown (0); the quantile is exact once it sits above it
+        q = float(np.quantile(vals, 1.0 - args.recovery, method="lower"))
+        if q >= probe or probe <= 0.5:
+            return float(np.floor(q * 1000) / 1000), len(vals)
+        probe -= 0.5
+
+
+def accuracy(rb_trig, plain_trig, w, rho_ii):
+    """Relative SNR loss of the hierarchy against the template method on the same GPU and block."""
+    p = {(int(t["tmpl"]), int(t["sample"]) // w): float(t["snr"]) for t in plain_trig}
+    r = {(int(t["tmpl"]), int(t["sample"]) // w): float(t["snr"]) for t in rb_trig}
+    matched = [(p[k], r[k]) for k in p if k in r]
+    loss = [(a - b) / a for a, b in matched]
+    # triggers of the flat search that the hierarchy missed although clearly above threshold
+    missed_clear = sum(1 for k, v in p.items() if k not in r and v > rho_ii * 1.001)
+    return dict(n_flat=len(p), n_hier=len(r), matched=len(matched),
+                recovery=(len(matched) / len(p)) if p else 1.0,
+                max_rel_snr_loss=max(loss) if loss else 0.0,
+                max_abs_rel_snr_err=max(abs(x) for x in loss) if loss else 0.0,
+                missed_above_threshold=missed_clear)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # the CPU baseline's process pool starts before the first GPU call
+    from paper_2110_13115_gb300 import inputs
+
+    wl = inputs.full(w=args.w, k=args.k, n_templates=args.templates, n=args.n, segment=rank)
+    pool, cores = None, 0
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = len(os.sched_getaffinity(0))
+        g0 = wl.grid
+        pool = mp.get_context("spawn").Pool(
+            cores, initializer=_oracle_init,
+            initargs=(wl.strain, wl.psd, g0.fs, g0.n, g0.f_low, wl.bank_spec.pn_order, wl.w, wl.rho_ii, wl.bank))
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2110_13115_gb300 import api, _native
+
+    _native.load()
+    g = wl.grid
+    T = len(wl.bank)
+    psd_d = torch.from_numpy(wl.psd).cuda()
+    strain_d = torch.from_numpy(wl.strain).cuda()
+    bank = api.Bank(wl.bank, g.fs, g.n, g.f_low, wl.bank_spec.pn_order)
+
+    t0 = time.perf_counter()
+    basis = api.rb_build(bank, psd_d, args.k, oversample=64, power_iters=1)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    trunc = 1.0 - basis.coeff.abs().pow(2).sum(1).double()
+    templates, _ = api.rb_templates(bank, psd_d)
+
+    wl_cal = inputs.full(w=args.w, k=args.k, n_templates=args.templates, n=args.n, segment=1000 + rank, n_inj=0)
+    rho_i, n_cal = calibrate_rho_i(api, basis, templates, psd_d, wl_cal, args, torch)
+
+    d = api.make_desc(g.fs, g.n, args.k, T, w=args.w, precision=args.precision, rho_i=rho_i, rho_ii=wl.rho_ii,
+                      cand_capacity=1 << 25, sample_offset=0, block_id=rank)
+    if args.precision != "fp32":
+        api.rb_pack_coeff(d, basis)
+    ws = api.workspace(d)
+    cap = 1 << 23
+    trig = torch.empty(cap * 24, dtype=torch.uint8, device="cuda")
+
+    def step():
+        return api.rb_filter(d, basis, strain_d, psd_d, capacity=cap, ws=ws, trig=trig)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = api.rb_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            _, nt = step()
+        e1.record()
+        torch.cuda.synchronize()
+    launches = (api.rb_kernel_launches() - launches0) // max(args.steps, 1)
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    secs_per_block = g.n // 2 / g.fs
+    value = world * T * secs_per_block / (ms / 1e3)
+    rb_trig = api.triggers_numpy(trig, nt)
+
+    # per-stage timing (CUDA events recorded by the library on the launching stream)
+    api.rb_profile_start()
+    for _ in range(args.steps):
+        step()
+    stage_ms, _ = api.rb_profile_stop()
+
+    # end to end through the public call: pinned host strain in, triggers out, every step
+    host_strain = torch.from_numpy(wl.strain).pin_memory()
+    host_trig = torch.empty(cap * 24, dtype=torch.uint8).pin_memory()
+    dev_in = torch.empty_like(strain_d)
+    h2d = host_strain.numel() * 4
+    d2h_total = 0
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter()
+    for _ in range(args.steps):
+        dev_in.copy_(host_strain, non_blocking=True)
+        _, n_e = api.rb_filter(d, basis, dev_in, psd_d, capacity=cap, ws=ws, trig=trig)
+        host_trig[: n_e * 24].copy_(trig[: n_e * 24], non_blocking=False)
+        d2h_total += n_e * 24 + 24
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t_e2e) * 1e3 / args.steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * T * secs_per_block / (e2e_ms / 1e3)
+
+    # the template method on the same GPU (comparator) and the accuracy gate against it
+    plain = None
+    acc = None
+    if not args.no_plain:
+        dp = api.make_desc(g.fs, g.n, 1, T, w=args.w, rho_ii=wl.rho_ii)
+        wsp = api.workspace(dp)
+        ptrig = torch.empty(cap * 24, dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            _, npl = api.rb_filter_plain(dp, templates, strain_d, psd_d, capacity=cap, ws=wsp, trig=ptrig)
+        torch.cuda.synchronize()
+        psteps = max(2, min(args.steps, 5))
+        e0.record()
+        for _ in range(psteps):
+            _, npl = api.rb_filter_plain(dp, templates, strain_d, psd_d, capacity=cap, ws=wsp, trig=ptrig)
+        e1.record()
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / psteps
+        plain = dict(ms_per_step=pms, value=world * T * secs_per_block / (pms / 1e3), unit=UNIT,
+                     impl="template method, fused Stockham FFT (this library)", speedup=pms / ms)
+        acc = accuracy(rb_trig, api.triggers_numpy(ptrig, npl), args.w, wl.rho_ii)
+        del wsp
+
+    # roofline of the dominant stage
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tensor = peaks.get("bf16_tflops_sustained", 1700.0)
+    smmax = peaks.get("sm_max_mhz", 2070.0)
+    half, nb = g.n // 2, g.n // (2 * args.w)
+    dom = max(("basis_filter", "first_stage"), key=lambda s: stage_ms[s])
+    if dom == "first_stage":
+        flops = 8.0 * T * args.k * nb
+        achieved = flops / (stage_ms[dom] / 1e3) / 1e12
+        if args.precision == "fp32":
+            peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
+            roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", kernel="k_stage1_simt",
+                        peak_source="152 SMs x 128 FP32 lanes x 2 flop x max SM clock")
+        else:
+            peak = tensor
+            roof = dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", kernel="k_stage1_tc",
+                        peak_source="MEASURED_PEAKS bf16_tflops_sustained (fp16 nominal rate = bf16)",
+                        issued_mma_flops_ratio=3.0 if "split" in args.precision else 1.0)
+        key, srcs = roof["kernel"], ("paper_2110_13115_gb300/csrc/gemm_tc.cu",)
+    else:
+        byts = args.k * (half * 8 + half * 8 + nb * 8)
+        achieved = byts / (stage_ms[dom] / 1e3) / 1e9
+        roof = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", kernel="k_pass_a+k_pass_b (basis)",
+                    peak_source="MEASURED_PEAKS hbm_gbs")
+        key, srcs = "basis_filter", ("paper_2110_13115_gb300/csrc/filter.cu", "paper_2110_13115_gb300/csrc/fft.cuh")
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_from_profiles(key, source_hash(*srcs))
+    roof["stage"] = dom
+
+    cpu = None
+    if pool is not None:
+        rate, done, wall, cores = oracle_rate(wl, args.cpu_seconds, pool=pool, cores=cores)
+        pool.close()
+        pool.join()
+        cpu = dict(value=rate, unit=UNIT, cores=cores, kind="oracle",
+                   sample=f"FP64 template method on {done} templates of the same block ({wall:.1f} s wall)")
+
+    clocks = clk.summary()
+    out = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+               ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+               data="synthetic",
+               config=dict(workload=wl.name, templates=T, block_samples=g.n, fs=g.fs, valid_seconds=secs_per_block,
+                           k=args.k, w=args.w, rho_I=rho_i, rho_II=wl.rho_ii, first_stage=args.precision,
+                           rho_I_calibration=f"noise-only block, {n_cal} flat triggers, recovery {args.recovery}",
+                           l2="inputs larger than L2: the basis alone is 537 MB per step",
+                           parallelism=f"replicas x{world} (one block per GPU)"),
+               roofline=roof, cpu_baseline=cpu,
+               e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h_total // args.steps),
+               gpu_launches=int(launches), clocks=clocks, stage_ms=stage_ms, plain_mf=plain, accuracy=acc,
+               basis=dict(build_s=build_s, max_truncation_loss=float(trunc.max()), mean_truncation_loss=float(trunc.mean()),
+                          oversample=64, power_iters=1),
+               n_triggers=int(nt))
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -212,6 +212,30 @@ int rb_filter_plain(const rb_filter_desc* desc, const float* templates, const fl
                     const double* psd, rb_trigger* trig, int64_t capacity, int64_t* n_trig,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/* Stages of rb_filter timed by the profiler (CUDA events recorded on the call's stream). */
+enum {
+  RB_STAGE_SETUP = 0,   /* status reset, twiddle tables, whitening weights */
+  RB_STAGE_WHITEN = 1,  /* a1 */
+  RB_STAGE_BASIS = 2,   /* a2 + a3 */
+  RB_STAGE_PACK = 3,    /* first-stage operand packing (16-bit precisions) */
+  RB_STAGE_FIRST = 4,   /* a4 contraction with fused threshold */
+  RB_STAGE_SECOND = 5,  /* a5 */
+  RB_STAGES = 6
+};
+
+/*
+ * rb_profile_start / rb_profile_stop - per-stage timing of rb_filter (measurement support; the
+ * paper reports in-situ wall time, Sec. IV.B.2). Between start and stop, every rb_filter call on
+ * the calling thread records a CUDA event at each stage boundary on its stream. stop synchronises
+ * those events and writes the mean milliseconds per stage into stage_ms[RB_STAGES] (host) and the
+ * number of profiled calls into *calls (host). Errors: RB_ERR_BAD_INPUT (stop without start).
+ */
+int rb_profile_start(void);
+int rb_profile_stop(double* stage_ms, int64_t* calls);
+
+/* Number of kernels this library has launched in this process (all entry points). */
+uint64_t rb_kernel_launches(void);
+
 /* A bank of closed-form stationary-phase chirps h(f) = f^(-7/6) exp(-i Psi(f)) (the
  * synthetic stand-in for the paper's IMRPhenomPv2 bank, Sec. III.B), with
  * Psi = -pi/4 + 3/(128 eta v^5) [1 + (20/9)(743/336 + 11 eta/4) v^2 + (4 beta - 16 pi) v^3],

@@ -20,6 +20,9 @@ RB_ERR_TIMEOUT = -4
 RB_ERR_CUDA = -5
 RB_ERR_UNSUPPORTED = -6
 
+RB_STAGES = 6
+STAGE_NAMES = ["setup", "whiten", "basis_filter", "pack", "first_stage", "second_stage"]
+
 RB_PREC_FP32 = 0
 RB_PREC_FP16_SPLIT = 1
 RB_PREC_BF16_SPLIT = 2
@@ -82,6 +85,9 @@ SIGNATURES = {
     "rb_stage2": (C.c_int, [_D, _B, _P, _P, C.c_int64, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_plain": (C.c_int, [_D, _P, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
+    "rb_profile_start": (C.c_int, []),
+    "rb_profile_stop": (C.c_int, [C.POINTER(C.c_double), _I64P]),
+    "rb_kernel_launches": (C.c_uint64, []),
     "rb_build_plan": (C.c_int, [C.POINTER(rb_bank_desc), C.c_int32, C.c_int32, C.POINTER(C.c_size_t),
                                 C.POINTER(C.c_size_t)]),
     "rb_templates": (C.c_int, [C.POINTER(rb_bank_desc), _P, _P, _P, _P, C.c_size_t, _P]),

@@ -221,3 +221,21 @@ def rb_build(bank: Bank, psd: torch.Tensor, k: int, oversample: int = 64, power_
     N.check("rb_build", rc)
     del ws
     return Basis(vec, coeff, bank.n, sigma2=s2, singular_values=np.array(sv[:]))
+
+
+# --- measurement support -------------------------------------------------------------------
+
+def rb_profile_start():
+    N.check("rb_profile_start", _lib().rb_profile_start())
+
+
+def rb_profile_stop():
+    """Mean milliseconds per rb_filter stage since rb_profile_start, and the call count."""
+    ms = (C.c_double * N.RB_STAGES)()
+    calls = C.c_int64(0)
+    N.check("rb_profile_stop", _lib().rb_profile_stop(ms, C.byref(calls)))
+    return dict(zip(N.STAGE_NAMES, ms[:])), calls.value
+
+
+def rb_kernel_launches() -> int:
+    return int(_lib().rb_kernel_launches())

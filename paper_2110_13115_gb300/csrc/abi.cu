@@ -9,8 +9,45 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include <atomic>
+#include <vector>
+
 namespace {
 thread_local char g_detail[512] = "";
+std::atomic<uint64_t> g_launches{0};
+
+// Per-thread profiler: one set of RB_STAGES + 1 events per profiled rb_filter call.
+struct Profiler {
+  bool on = false;
+  std::vector<std::vector<cudaEvent_t>> sets;
+};
+thread_local Profiler g_prof;
+
+struct StageMarks {
+  std::vector<cudaEvent_t>* ev = nullptr;
+  cudaStream_t st = nullptr;
+  int last = -1;
+  void begin(cudaStream_t s) {
+    if (!g_prof.on) return;
+    g_prof.sets.emplace_back(RB_STAGES + 1, nullptr);
+    ev = &g_prof.sets.back();
+    for (auto& e : *ev) cudaEventCreate(&e);
+    st = s;
+    cudaEventRecord((*ev)[0], st);
+    last = 0;
+  }
+  // mark the start of `stage` (= the end of the previous one); skipped stages get zero duration
+  void to(int stage) {
+    if (!ev) return;
+    for (int i = last + 1; i <= stage; ++i) cudaEventRecord((*ev)[i], st);
+    last = std::max(last, stage);
+  }
+  void finish() {
+    if (!ev) return;
+    for (int i = last + 1; i <= RB_STAGES; ++i) cudaEventRecord((*ev)[i], st);
+    last = RB_STAGES;
+  }
+};
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -21,6 +58,8 @@ struct Status {
   unsigned long long trig;
 };
 }  // namespace
+
+void rb_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void rb_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   snprintf(g_detail, sizeof(g_detail), "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what,
@@ -116,6 +155,9 @@ void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws
       ws->bop_lo = split ? take(plane) : nullptr;
     }
     ws->cand = (rb_candidate*)take(sizeof(rb_candidate) * (size_t)std::max<int64_t>(d.cand_capacity, 1));
+    ws->cand_sorted = (rb_candidate*)take(sizeof(rb_candidate) * (size_t)std::max<int64_t>(d.cand_capacity, 1));
+    ws->bin_count = (unsigned*)take(sizeof(unsigned) * (size_t)(g.n_bins + 1));
+    ws->bin_start = (unsigned*)take(sizeof(unsigned) * (size_t)(g.n_bins + 1));
   }
   ws->total = off;
 }
@@ -184,6 +226,40 @@ const char* rb_strerror(int status) {
 const char* rb_last_error_detail(void) { return g_detail; }
 
 int rb_version(void) { return 100; }
+
+uint64_t rb_kernel_launches(void) { return g_launches.load(); }
+
+int rb_profile_start(void) {
+  g_prof.on = true;
+  g_prof.sets.clear();
+  return RB_OK;
+}
+
+int rb_profile_stop(double* stage_ms, int64_t* calls) {
+  if (!g_prof.on) {
+    set_detail("rb_profile_stop without rb_profile_start");
+    return RB_ERR_BAD_INPUT;
+  }
+  g_prof.on = false;
+  std::vector<double> acc(RB_STAGES, 0.0);
+  int rc = RB_OK;
+  for (auto& set : g_prof.sets) {
+    if (cudaEventSynchronize(set[RB_STAGES]) != cudaSuccess) rc = RB_ERR_CUDA;
+    for (int i = 0; i < RB_STAGES && rc == RB_OK; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, set[i], set[i + 1]) != cudaSuccess) rc = RB_ERR_CUDA;
+      acc[i] += ms;
+    }
+    for (auto e : set) cudaEventDestroy(e);
+  }
+  const int64_t n = (int64_t)g_prof.sets.size();
+  g_prof.sets.clear();
+  if (calls) *calls = n;
+  if (stage_ms)
+    for (int i = 0; i < RB_STAGES; ++i) stage_ms[i] = n ? acc[i] / n : 0.0;
+  if (rc) set_detail("profiling events failed");
+  return rc;
+}
 
 int rb_filter_plan(const rb_filter_desc* desc, rb_filter_sizes* out) {
   if (!desc || !out) {
@@ -258,14 +334,18 @@ int rb_pack_coeff(const rb_filter_desc* desc, const rb_basis* basis, void* out, 
 }
 
 static int run_stage1(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-                      const float2* bavg, rb_candidate* cand, cudaStream_t st) {
-  if (d.precision == RB_PREC_FP32) return stage1_simt(d, b, g, ws, bavg, cand, st);
+                      const float2* bavg, rb_candidate* cand, cudaStream_t st, StageMarks* mk = nullptr) {
+  if (d.precision == RB_PREC_FP32) {
+    if (mk) mk->to(RB_STAGE_FIRST);
+    return stage1_simt(d, b, g, ws, bavg, cand, st);
+  }
   if (!b.coeff_op || b.coeff_op_precision != d.precision) {
     set_detail("coeff_op missing or packed for precision %d (need %d)", b.coeff_op_precision, d.precision);
     return RB_ERR_BAD_INPUT;
   }
   int rc = pack_beta(d, g, bavg, ws.bop_hi, ws.bop_lo, st);
   if (rc) return rc;
+  if (mk) mk->to(RB_STAGE_FIRST);
   return stage1_tc(d, b, g, ws, cand, st);
 }
 
@@ -284,6 +364,10 @@ int rb_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* be
   if ((rc = run_stage1(*desc, *basis, g, ws, (const float2*)beta_avg, cand, st))) return rc;
   Status s;
   if ((rc = read_status(ws, &s, st))) return rc;
+  if (s.flags & RB_FLAG_TIMEOUT) {
+    set_detail("a device-side wait of the first stage timed out");
+    return RB_ERR_TIMEOUT;
+  }
   *n_cand = (int64_t)s.cand;
   return (int64_t)s.cand > desc->cand_capacity ? RB_ERR_OVERFLOW : RB_OK;
 }
@@ -323,18 +407,28 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
     set_detail("NULL array or negative capacity");
     return RB_ERR_BAD_INPUT;
   }
+  StageMarks mk;
+  mk.begin(st);
   if ((rc = init_tables(g, ws, psd, desc->fs, st))) return rc;
+  mk.to(RB_STAGE_WHITEN);
   if ((rc = whiten(g, ws, strain, ws.shat, st))) return rc;
+  mk.to(RB_STAGE_BASIS);
   if ((rc = bank_filter(g, ws, (const float2*)basis->vectors, desc->k, ws.shat, ws.beta, ws.bavg, desc->w, st)))
     return rc;
-  if ((rc = run_stage1(*desc, *basis, g, ws, ws.bavg, ws.cand, st))) return rc;
-  if ((rc = stage2(*desc, *basis, ws.beta, ws.cand, ws.cand_count, 0, trig, capacity, ws.trig_count, st)))
-    return rc;
+  mk.to(RB_STAGE_PACK);
+  if ((rc = run_stage1(*desc, *basis, g, ws, ws.bavg, ws.cand, st, &mk))) return rc;
+  mk.to(RB_STAGE_SECOND);
+  if ((rc = stage2_bucketed(*desc, *basis, g, ws, trig, capacity, st))) return rc;
+  mk.finish();
   Status s;
   if ((rc = read_status(ws, &s, st))) return rc;
   if (s.flags & RB_FLAG_BAD_PSD) {
     set_detail("PSD not finite and positive on 0 < j < n/2");
     return RB_ERR_BAD_INPUT;
+  }
+  if (s.flags & RB_FLAG_TIMEOUT) {
+    set_detail("a device-side wait of the first stage timed out");
+    return RB_ERR_TIMEOUT;
   }
   if ((int64_t)s.cand > desc->cand_capacity) {
     *n_trig = -1;

@@ -14,8 +14,11 @@
     }                                                       \
   } while (0)
 
+void rb_count_launch();
+
 #define RB_LAUNCH_CHECK()                                                     \
   do {                                                                        \
+    rb_count_launch();                                                        \
     cudaError_t _e = cudaGetLastError();                                      \
     if (_e != cudaSuccess) {                                                  \
       rb_set_last_cuda_error(_e, "kernel launch", __FILE__, __LINE__);        \

@@ -1,11 +1,430 @@
-// First-stage reconstruction on tcgen05 tensor cores (placeholder until the kernel lands).
+// First-stage reconstruction on tcgen05 tensor cores (arXiv:2110.13115 Sec. III.C first stage,
+// Sec. III.E "multiplying beta^avg and D"): z_avg[t, i] = sum_k conj(a_tk) beta_avg_k[i] as one
+// real contraction over K = 2k,
+//   rows 2t   [Re a_t, Im a_t]   . [Re b_i, Im b_i] = Re z_avg[t, i]
+//   rows 2t+1 [-Im a_t, Re a_t]  . [Re b_i, Im b_i] = Im z_avg[t, i],
+// with 16-bit operands (one plane, or hi + lo planes with three products hi.hi + hi.lo + lo.hi)
+// and FP32 accumulators in tensor memory. The epilogue squares, pairs the Re/Im rows across
+// neighbouring lanes, tests |z_avg|^2 >= rho_I^2 and appends candidates; the T x bins array
+// never reaches global memory.
+//
+// Persistent kernel, one CTA per SM, 192 threads:
+//   warp 0  : TMA producer (one thread) - 128B-swizzled K-major tiles of A (128 x 64) and
+//             B (256 x 64) per plane into a STAGES-deep shared-memory ring;
+//   warp 1  : tensor-memory allocation (512 columns) and the MMA issuer (one thread),
+//             M = 128, N = 256, K = 16 per instruction, two accumulator buffers;
+//   warps 2-5: epilogue, each reading its 32-lane quarter of tensor memory.
+// Every mbarrier wait is bounded (1 s of %globaltimer); a timeout sets RB_FLAG_TIMEOUT, makes the
+// other roles stop, waits (bounded) for the copies and products in flight, frees tensor memory
+// and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
-namespace rb {
-int stage1_tc(const rb_filter_desc&, const rb_basis&, const Geometry&, const Workspace&, rb_candidate*,
-              cudaStream_t) {
-  set_detail("tensor-core first stage not built");
-  return RB_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+struct TcParams {
+  int T;          // templates (rows of A = 2T)
+  int N;          // valid bins (rows of B)
+  int KB;         // K blocks of 64
+  int num_m, num_n;
+  float thr2;
+  int bin0;
+  int block_id;
+  rb_candidate* cand;
+  unsigned long long* counter;
+  long long cap;
+  unsigned* flags;
+  uint32_t idesc;
+};
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase of parity `parity` to complete; false on abort or after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 64-bit shared-memory matrix descriptor: K-major tile written by TMA with 128-byte swizzle,
+// rows 128 B apart, 8-row core groups 1024 B apart (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]),
+        "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]),
+        "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int NPLANES, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_stage1_tc(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+                const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1, TcParams p) {
+  constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  constexpr uint32_t STAGE_BYTES = NPLANES * (A_BYTES + B_BYTES);
+  extern __shared__ uint8_t dsmem[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t smem0 = (saddr(dsmem) + 1023u) & ~1023u;
+  const int num_tiles = p.num_m * p.num_n;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);
+    }
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  auto fail = [&]() {
+    abort_flag = 1;
+    atomicOr(p.flags, (unsigned)RB_FLAG_TIMEOUT);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int used = 0;  // stages that received at least one load
+      for (int tile = blockIdx.x; tile < num_tiles && !abort_flag; tile += gridDim.x) {
+        const int mb = tile % p.num_m, nb = tile / p.num_m;
+        for (int kb = 0; kb < p.KB; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1, &abort_flag)) {
+            fail();
+            break;
+          }
+          const uint32_t sb = smem0 + stage * STAGE_BYTES;
+          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          tma_load(sb, &tmA0, &full[stage], kb * BK, mb * BM);
+          if (NPLANES == 2) tma_load(sb + A_BYTES, &tmA1, &full[stage], kb * BK, mb * BM);
+          tma_load(sb + NPLANES * A_BYTES, &tmB0, &full[stage], kb * BK, nb * BN);
+          if (NPLANES == 2) tma_load(sb + NPLANES * A_BYTES + B_BYTES, &tmB1, &full[stage], kb * BK, nb * BN);
+          used = used < STAGES ? used + 1 : STAGES;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      // copies in flight land before the CTA may exit: the last load of each used stage
+      for (int i = 0; i < used; ++i) {
+        if (--stage < 0) {
+          stage = STAGES - 1;
+          phase ^= 1;
+        }
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(&full[stage], phase) && gtimer() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      bool issued = false;
+      for (int tile = blockIdx.x; tile < num_tiles && !abort_flag; tile += gridDim.x) {
+        if (!mbar_wait(&tempty[acc], acc_phase ^ 1, &abort_flag)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        bool ok = true;
+        for (int kb = 0; kb < p.KB; ++kb) {
+          if (!mbar_wait(&full[stage], phase, &abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem0 + stage * STAGE_BYTES;
+          const uint32_t a1 = a0 + A_BYTES;
+          const uint32_t b0 = a0 + NPLANES * A_BYTES;
+          const uint32_t b1 = b0 + B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint32_t off = kk * 32;
+            tc_mma(d, sw128_desc(a0 + off), sw128_desc(b0 + off), p.idesc, (kb | kk) != 0);
+            if (NPLANES == 2) {
+              tc_mma(d, sw128_desc(a0 + off), sw128_desc(b1 + off), p.idesc, 1);
+              tc_mma(d, sw128_desc(a1 + off), sw128_desc(b0 + off), p.idesc, 1);
+            }
+          }
+          issued = true;
+          tc_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        tc_commit(&tfull[acc]);
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
+      }
+      if (issued) {
+        // every product issued so far has completed before tensor memory is released
+        tc_commit(&drain);
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(&drain, 0) && gtimer() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else {
+    const int q = warp & 3;  // tensor-memory lane quarter this warp may access
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    const unsigned full_mask = 0xffffffffu;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+      if (!mbar_wait(&tfull[acc], acc_phase, &abort_flag)) {
+        if (lane == 0) fail();
+        break;
+      }
+      tc_fence_after();
+      const int mb = tile % p.num_m, nb = tile / p.num_m;
+      const int row = mb * BM + q * 32 + lane;
+      const int t = row >> 1;
+      const bool even = (lane & 1) == 0;
+      const bool trow = even && t < p.T;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tc_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c0), v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float p2 = v[j] * v[j];
+          p2 += __shfl_xor_sync(full_mask, p2, 1);
+          const int col = nb * BN + c0 + j;
+          const bool hit = trow && col < p.N && p2 >= p.thr2;
+          const unsigned mask = __ballot_sync(full_mask, hit);
+          if (mask) {
+            const int leader = __ffs(mask) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(p.counter, (unsigned long long)__popc(mask));
+            base = __shfl_sync(full_mask, base, leader);
+            if (hit) {
+              const unsigned long long idx = base + __popc(mask & lt_mask);
+              if ((long long)idx < p.cap) {
+                rb_candidate c;
+                c.tmpl = t;
+                c.bin = p.bin0 + col;
+                c.snr_avg = sqrtf(p2);
+                c.block = p.block_id;
+                p.cand[idx] = c;
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// --- host side --------------------------------------------------------------------------------
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(ptr);
+  });
+  return fn;
+}
+
+// 2D map over a [rows][kp] 16-bit matrix, box of 64 (K) x box_rows, 128-byte swizzle, zero fill.
+int make_map(CUtensorMap* m, const void* base, bool bf16, int64_t kp, int64_t rows, int box_rows) {
+  EncodeTiled enc = encode_fn();
+  if (!enc) {
+    rb::set_detail("cuTensorMapEncodeTiled unavailable from the driver");
+    return RB_ERR_CUDA;
+  }
+  if (((uintptr_t)base & 15) || (kp * 2) % 16) {
+    rb::set_detail("operand base or row pitch not 16-byte aligned");
+    return RB_ERR_BAD_INPUT;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    rb::set_detail("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return RB_ERR_CUDA;
+  }
+  return RB_OK;
+}
+
+template <int NPLANES, int STAGES>
+int launch_tc(const CUtensorMap* maps, const TcParams& p, cudaStream_t st) {
+  constexpr int smem = STAGES * NPLANES * (BM * BK * 2 + BN * BK * 2) + 1024;
+  auto kern = k_stage1_tc<NPLANES, STAGES>;
+  RB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int dev = 0, sms = 0;
+  RB_CUDA_TRY(cudaGetDevice(&dev));
+  RB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int tiles = p.num_m * p.num_n;
+  const int grid = std::max(1, std::min(tiles, sms));
+  kern<<<grid, kThreads, smem, st>>>(maps[0], maps[1], maps[2], maps[3], p);
+  RB_LAUNCH_CHECK();
+  return RB_OK;
+}
+
+}  // namespace
+
+namespace rb {
+
+int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws, rb_candidate* cand,
+              cudaStream_t st) {
+  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
+  const bool bf = d.precision == RB_PREC_BF16 || d.precision == RB_PREC_BF16_SPLIT;
+  const int64_t M = 2 * (int64_t)d.n_templates;
+  CUtensorMap maps[4];
+  const uint16_t* a0 = (const uint16_t*)b.coeff_op;
+  const uint16_t* a1 = split ? a0 + M * g.kp : a0;
+  int rc;
+  if ((rc = make_map(&maps[0], a0, bf, g.kp, M, BM))) return rc;
+  if ((rc = make_map(&maps[1], a1, bf, g.kp, M, BM))) return rc;
+  if ((rc = make_map(&maps[2], ws.bop_hi, bf, g.kp, g.n_bins, BN))) return rc;
+  if ((rc = make_map(&maps[3], split ? ws.bop_lo : ws.bop_hi, bf, g.kp, g.n_bins, BN))) return rc;
+  TcParams p;
+  p.T = d.n_templates;
+  p.N = (int)g.n_bins;
+  p.KB = g.kp / BK;
+  p.num_m = (int)((M + BM - 1) / BM);
+  p.num_n = (int)((g.n_bins + BN - 1) / BN);
+  p.thr2 = d.rho_i * d.rho_i;
+  p.bin0 = (int)g.n_bins;
+  p.block_id = d.block_id;
+  p.cand = cand;
+  p.counter = ws.cand_count;
+  p.cap = d.cand_capacity;
+  p.flags = ws.flags;
+  const uint32_t fmt = bf ? 1u : 0u;
+  p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  return split ? launch_tc<2, 2>(maps, p, st) : launch_tc<1, 4>(maps, p, st);
+}
+
 }  // namespace rb

@@ -41,6 +41,9 @@ struct Workspace {
   void* bop_hi = nullptr;     // [n_bins][kp] 16-bit
   void* bop_lo = nullptr;     // [n_bins][kp] 16-bit (split precisions)
   rb_candidate* cand = nullptr;
+  rb_candidate* cand_sorted = nullptr;  // candidates grouped by bin for the second stage
+  unsigned* bin_count = nullptr;        // [n_bins + 1] per-bin counts, then fill cursors
+  unsigned* bin_start = nullptr;        // [n_bins + 1] exclusive prefix sums
   size_t total = 0;
 };
 
@@ -64,6 +67,8 @@ int pack_beta(const rb_filter_desc& d, const Geometry& g, const float2* bavg, vo
 int pack_coeff(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, void* out, cudaStream_t st);
 int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
               rb_candidate* cand, cudaStream_t st);
+int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
+                    rb_trigger* trig, int64_t cap, cudaStream_t st);
 int stage2(const rb_filter_desc& d, const rb_basis& b, const float2* beta, const rb_candidate* cand,
            const unsigned long long* dev_count, int64_t host_count, rb_trigger* trig, int64_t cap,
            unsigned long long* counter, cudaStream_t st);

@@ -259,12 +259,13 @@ def tiny(w: int = 8, k: int = 16, noise: bool = True, n_templates: int = 64) -> 
                          snr_range=10.0, noise=noise)
 
 
-def full(w: int = 8, k: int = 256, n_templates: int = 10000, n_inj: int = 20) -> Workload:
+def full(w: int = 8, k: int = 256, n_templates: int = 10000, n_inj: int = 20, segment: int = 0,
+         noise: bool = True, n: int = 524288) -> Workload:
     """10,000 templates (masses 3-50, aligned spins, 1.5PN), 256 s at 2048 Hz, 20 injections SNR 5-20."""
-    grid = Grid(fs=2048.0, n=524288, f_low=30.0)
+    grid = Grid(fs=2048.0, n=n, f_low=30.0)
     spec = BankSpec(n_templates, 3.0, 50.0, 0.5, 3)
-    return make_workload("full-10000x256s@2048Hz", grid, spec, k=k, w=w, rho_ii=5.0, n_inj=n_inj,
-                         snr_range=(5.0, 20.0), min_sep=4.0)
+    return make_workload(f"full-{n_templates}x{int(n / 2048)}s@2048Hz", grid, spec, k=k, w=w, rho_ii=5.0,
+                         n_inj=n_inj, snr_range=(5.0, 20.0), min_sep=4.0, segment=segment, noise=noise)
 
 
 def scaled(name: str, fs: float, n: int, n_templates: int, m_range=(3.0, 50.0), chi_max=0.5, pn_order=3,
