@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--rho-i", type=float, default=None, help="fixed first-stage threshold (skips calibration)")
     return p.parse_args()
 
 
@@ -294,11 +295,18 @@ def main():
     basis = api.rb_build(bank, psd_d, args.k, oversample=64, power_iters=1)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
-    trunc = 1.0 - basis.coeff.abs().pow(2).sum(1).double()
-    templates, _ = api.rb_templates(bank, psd_d)
+    captured = basis.coeff.abs().pow(2).double().cumsum(1)
+    trunc = 1.0 - captured[:, -1]
+    loss_by_k = {int(kk): float(1.0 - captured[:, kk - 1].min()) for kk in (64, 128, 192, 256, 320, 384, 448, 512)
+                 if kk <= args.k}
+    need_templates = not args.no_plain or args.rho_i is None
+    templates = api.rb_templates(bank, psd_d)[0] if need_templates else None
 
-    wl_cal = inputs.full(w=args.w, k=args.k, n_templates=args.templates, n=args.n, segment=1000 + rank, n_inj=0)
-    rho_i, n_cal = calibrate_rho_i(api, basis, templates, psd_d, wl_cal, args, torch)
+    if args.rho_i is None:
+        wl_cal = inputs.full(w=args.w, k=args.k, n_templates=args.templates, n=args.n, segment=1000 + rank, n_inj=0)
+        rho_i, n_cal = calibrate_rho_i(api, basis, templates, psd_d, wl_cal, args, torch)
+    else:
+        rho_i, n_cal = args.rho_i, 0
 
     d = api.make_desc(g.fs, g.n, args.k, T, w=args.w, precision=args.precision, rho_i=rho_i, rho_ii=wl.rho_ii,
                       cand_capacity=1 << 25, sample_offset=0, block_id=rank)
@@ -440,7 +448,7 @@ def main():
                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h_total // args.steps),
                gpu_launches=int(launches), clocks=clocks, stage_ms=stage_ms, plain_mf=plain, accuracy=acc,
                basis=dict(build_s=build_s, max_truncation_loss=float(trunc.max()), mean_truncation_loss=float(trunc.mean()),
-                          oversample=64, power_iters=1),
+                          max_truncation_loss_by_k=loss_by_k, oversample=64, power_iters=1),
                n_triggers=int(nt))
     if rank == 0:
         print(json.dumps(out))

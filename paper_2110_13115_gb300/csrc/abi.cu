@@ -385,9 +385,17 @@ int rb_stage2(const rb_filter_desc* desc, const rb_basis* basis, const float* be
     set_detail("NULL array or negative count");
     return RB_ERR_BAD_INPUT;
   }
-  if (n_cand > 0 &&
-      (rc = stage2(*desc, *basis, (const float2*)beta, cand, nullptr, n_cand, trig, capacity, ws.trig_count, st)))
-    return rc;
+  if (n_cand > desc->cand_capacity) {
+    set_detail("n_cand %lld exceeds desc->cand_capacity %lld", (long long)n_cand, (long long)desc->cand_capacity);
+    return RB_ERR_BAD_INPUT;
+  }
+  if (n_cand > 0) {
+    const unsigned long long cnt = (unsigned long long)n_cand;
+    RB_CUDA_TRY(cudaMemcpyAsync(ws.cand, cand, sizeof(rb_candidate) * n_cand, cudaMemcpyDeviceToDevice, st));
+    RB_CUDA_TRY(cudaMemcpyAsync(ws.cand_count, &cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
+    RB_CUDA_TRY(cudaStreamSynchronize(st));  // cnt lives on this stack frame
+    if ((rc = stage2_bucketed(*desc, *basis, g, ws, (const float2*)beta, trig, capacity, st))) return rc;
+  }
   Status s;
   if ((rc = read_status(ws, &s, st))) return rc;
   *n_trig = (int64_t)s.trig;
@@ -418,7 +426,7 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
   mk.to(RB_STAGE_PACK);
   if ((rc = run_stage1(*desc, *basis, g, ws, ws.bavg, ws.cand, st, &mk))) return rc;
   mk.to(RB_STAGE_SECOND);
-  if ((rc = stage2_bucketed(*desc, *basis, g, ws, trig, capacity, st))) return rc;
+  if ((rc = stage2_bucketed(*desc, *basis, g, ws, ws.beta, trig, capacity, st))) return rc;
   mk.finish();
   Status s;
   if ((rc = read_status(ws, &s, st))) return rc;

@@ -1,7 +1,6 @@
 // Hot path of the hierarchical reduced-basis matched filter (arXiv:2110.13115, Sec. III.C/E):
 //   a1 whitening forward FFT, a2+a3 basis SNR series with bin averages, the template-method
-//   comparator, the FP32 first stage, operand packing for the tensor-core first stage, and
-//   the second stage. Host entry points of the C ABI (include/rbmf.h) are at the bottom.
+//   comparator, the FP32 first stage, and operand packing for the tensor-core first stage.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -292,77 +291,6 @@ __global__ void __launch_bounds__(256) k_stage1_simt(const float2* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------------------
-// Second stage (Sec. III.C): one warp per candidate, lanes split the basis index k; the W
-// full-rate samples of the bin are reduced across the warp; arg-max (first on ties).
-template <int W>
-__global__ void __launch_bounds__(256) k_stage2(const float2* __restrict__ coeff, int ldk,
-                                                const float2* __restrict__ beta, int k, int T, int64_t half,
-                                                const rb_candidate* __restrict__ cand,
-                                                const unsigned long long* dev_count, int64_t cand_cap,
-                                                int64_t host_count, float thr2, int64_t sample_offset,
-                                                rb_trigger* trig, unsigned long long* counter,
-                                                int64_t cap) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int64_t ncand = host_count;
-  if (dev_count) ncand = (int64_t)min((unsigned long long)cand_cap, *dev_count);
-  for (int64_t ci = gw; ci < ncand; ci += nw) {
-    const rb_candidate cd = cand[ci];
-    // caller-provided candidates: skip anything outside the valid bins or the bank
-    if (cd.tmpl < 0 || cd.tmpl >= T || (int64_t)cd.bin * W < half || (int64_t)cd.bin * W >= 2 * half) continue;
-    const int64_t mb = (int64_t)cd.bin * W - half;
-    float2 acc[W];
-#pragma unroll
-    for (int r = 0; r < W; ++r) acc[r] = make_float2(0.f, 0.f);
-    const float2* arow = coeff + (int64_t)cd.tmpl * ldk;
-    for (int kk = lane; kk < k; kk += 32) {
-      const float2 av = __ldg(arow + kk);
-      const float2* bp = beta + (int64_t)kk * half + mb;
-#pragma unroll
-      for (int r = 0; r < W; ++r) {
-        const float2 bv = __ldg(bp + r);
-        acc[r].x = fmaf(av.x, bv.x, fmaf(av.y, bv.y, acc[r].x));
-        acc[r].y = fmaf(av.x, bv.y, fmaf(-av.y, bv.x, acc[r].y));
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < W; ++r)
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, off);
-        acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, off);
-      }
-    if (lane == 0) {
-      int best = 0;
-      float r2b = cabs2(acc[0]);
-      float2 zb = acc[0];
-#pragma unroll
-      for (int r = 1; r < W; ++r) {
-        const float r2 = cabs2(acc[r]);
-        if (r2 > r2b) {
-          r2b = r2;
-          best = r;
-          zb = acc[r];
-        }
-      }
-      if (r2b >= thr2) {
-        const unsigned long long idx = atomicAdd(counter, 1ull);
-        if ((int64_t)idx < cap) {
-          rb_trigger t;
-          t.sample = sample_offset + (int64_t)cd.bin * W + best;
-          t.tmpl = cd.tmpl;
-          t.block = cd.block;
-          t.snr = sqrtf(r2b);
-          t.phase = atan2f(zb.y, zb.x);
-          trig[idx] = t;
-        }
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------------------
 // Operand packing for the tensor-core first stage (16-bit planes, hi then lo).
 template <typename T16>
 __device__ __forceinline__ T16 to16(float x);
@@ -518,22 +446,6 @@ static int launch_b(const rb::Geometry& g, const PassBArgs& a, const rb::Tables&
   return RB_ERR_UNSUPPORTED;
 }
 
-template <int W>
-static int launch_stage2_W(const rb_filter_desc& d, const rb_basis& b, const float2* beta,
-                           const rb_candidate* cand, const unsigned long long* dev_count,
-                           int64_t host_count, rb_trigger* trig, int64_t cap,
-                           unsigned long long* counter, cudaStream_t st) {
-  const int64_t half = d.n / 2;
-  const int threads = 256;
-  int64_t blocks = dev_count ? 152 * 8 : std::max<int64_t>(1, (host_count + 7) / 8);
-  blocks = std::min<int64_t>(blocks, 152 * 64);
-  k_stage2<W><<<(unsigned)blocks, threads, 0, st>>>(
-      reinterpret_cast<const float2*>(b.coeff), b.k, beta, d.k, d.n_templates, half, cand, dev_count,
-      d.cand_capacity, host_count, d.rho_ii * d.rho_ii, d.sample_offset, trig, counter, cap);
-  RB_LAUNCH_CHECK();
-  return RB_OK;
-}
-
 }  // namespace
 
 // =======================================================================================
@@ -625,19 +537,6 @@ int pack_beta(const rb_filter_desc& d, const Geometry& g, const float2* bavg, vo
     k_pack_beta<__half><<<grid, 256, 0, st>>>(bavg, d.k, nb, g.kp, (__half*)hi, (__half*)lo);
   RB_LAUNCH_CHECK();
   return RB_OK;
-}
-
-int stage2(const rb_filter_desc& d, const rb_basis& b, const float2* beta, const rb_candidate* cand,
-           const unsigned long long* dev_count, int64_t host_count, rb_trigger* trig, int64_t cap,
-           unsigned long long* counter, cudaStream_t st) {
-  switch (d.w) {
-    case 1: return launch_stage2_W<1>(d, b, beta, cand, dev_count, host_count, trig, cap, counter, st);
-    case 2: return launch_stage2_W<2>(d, b, beta, cand, dev_count, host_count, trig, cap, counter, st);
-    case 4: return launch_stage2_W<4>(d, b, beta, cand, dev_count, host_count, trig, cap, counter, st);
-    case 8: return launch_stage2_W<8>(d, b, beta, cand, dev_count, host_count, trig, cap, counter, st);
-    case 16: return launch_stage2_W<16>(d, b, beta, cand, dev_count, host_count, trig, cap, counter, st);
-  }
-  return RB_ERR_BAD_INPUT;
 }
 
 int pack_coeff(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, void* out, cudaStream_t st) {

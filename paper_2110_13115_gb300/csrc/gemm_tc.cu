@@ -8,12 +8,12 @@
 // neighbouring lanes, tests |z_avg|^2 >= rho_I^2 and appends candidates; the T x bins array
 // never reaches global memory.
 //
-// Persistent kernel, one CTA per SM, 192 threads:
+// Persistent kernel, one CTA per SM, 320 threads:
 //   warp 0  : TMA producer (one thread) - 128B-swizzled K-major tiles of A (128 x 64) and
 //             B (256 x 64) per plane into a STAGES-deep shared-memory ring;
 //   warp 1  : tensor-memory allocation (512 columns) and the MMA issuer (one thread),
 //             M = 128, N = 256, K = 16 per instruction, two accumulator buffers;
-//   warps 2-5: epilogue, each reading its 32-lane quarter of tensor memory.
+//   warps 2-9: epilogue, two per 32-lane quarter of tensor memory (half the columns each).
 // Every mbarrier wait is bounded (1 s of %globaltimer); a timeout sets RB_FLAG_TIMEOUT, makes the
 // other roles stop, waits (bounded) for the copies and products in flight, frees tensor memory
 // and returns.
@@ -30,7 +30,7 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;  // producer warp, MMA warp, 8 epilogue warps
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitNs = 1000000000ull;
 
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 4);
+      mbar_init(&tempty[a], 8);
     }
     mbar_init(&drain, 1);
     abort_flag = 0;
@@ -269,7 +269,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    const int q = warp & 3;  // tensor-memory lane quarter this warp may access
+    // two warps per tensor-memory lane quarter, each owning half of the tile's columns
+    const int q = warp & 3;
+    const int cbase = ((warp - 2) >> 2) * (BN / 2);
     int acc = 0;
     uint32_t acc_phase = 0;
     const unsigned full_mask = 0xffffffffu;
@@ -286,14 +288,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool even = (lane & 1) == 0;
       const bool trow = even && t < p.T;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = cbase; c0 < cbase + BN / 2; c0 += 32) {
         float v[32];
         tc_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c0), v);
+        // |z|^2 of the (Re, Im) row pair: rows 2t and 2t+1 sit in neighbouring lanes
+        float pmax = 0.f;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          float p2 = v[j] * v[j];
-          p2 += __shfl_xor_sync(full_mask, p2, 1);
-          const int col = nb * BN + c0 + j;
+          v[j] = v[j] * v[j];
+          v[j] += __shfl_xor_sync(full_mask, v[j], 1);
+          pmax = fmaxf(pmax, v[j]);
+        }
+        const int col0 = nb * BN + c0;
+        if (!__any_sync(full_mask, trow && col0 < p.N && pmax >= p.thr2)) continue;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float p2 = v[j];
+          const int col = col0 + j;
           const bool hit = trow && col < p.N && p2 >= p.thr2;
           const unsigned mask = __ballot_sync(full_mask, hit);
           if (mask) {

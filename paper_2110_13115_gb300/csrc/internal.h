@@ -68,9 +68,6 @@ int pack_coeff(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, vo
 int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
               rb_candidate* cand, cudaStream_t st);
 int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-                    rb_trigger* trig, int64_t cap, cudaStream_t st);
-int stage2(const rb_filter_desc& d, const rb_basis& b, const float2* beta, const rb_candidate* cand,
-           const unsigned long long* dev_count, int64_t host_count, rb_trigger* trig, int64_t cap,
-           unsigned long long* counter, cudaStream_t st);
+                    const float2* beta, rb_trigger* trig, int64_t cap, cudaStream_t st);
 
 }  // namespace rb

@@ -1,9 +1,19 @@
-// Second stage of the hierarchy (arXiv:2110.13115 Sec. III.C, "finer reconstruction for every
-// sample inside all the triggering bins"; Sec. III.E custom kernel), grouped by bin:
-// first-stage candidates are bucketed by bin (count, scan, scatter), then one CTA per bin stages
-// the k x w window of beta in shared memory once and every warp reconstructs one candidate
-// template over the window, z[m] = sum_k conj(a_tk) beta_k[m] in FP32, keeping the arg-max
-// (first on ties) when |z| >= rho_II.
+// Second stage of the hierarchy (arXiv:2110.13115 Sec. III.C, full-resolution reconstruction of
+// every sample inside the triggering bins; Sec. III.E custom kernel), grouped by bin.
+//
+// 1. First-stage candidates are bucketed by bin: per-bin counts (warp-aggregated atomics), an
+//    exclusive scan, and a scatter.
+// 2. One CTA per bin stages the bin's k x w window of beta once, as 16-bit hi + lo tensor-core
+//    fragments of the real contraction
+//        B[kk][2r]   = kk < k ? Re beta_kk[m0 + r] :  Im beta_(kk-k)[m0 + r]
+//        B[kk][2r+1] = kk < k ? Im beta_kk[m0 + r] : -Re beta_(kk-k)[m0 + r],
+//    so that [Re a_t, Im a_t] . B gives (Re, Im) of z_t[m0 + r] = sum_k conj(a_tk) beta_k[m0 + r].
+//    Each warp reconstructs 16 candidates at a time with mma.sync m16n8k16 (FP16 in, FP32
+//    accumulate) using three products hi.hi + hi.lo + lo.hi, which keeps the result at FP32
+//    accuracy; coefficients are read in FP32 and split on the fly.
+// 3. The arg-max over the bin's w samples (first on ties) is kept when |z| >= rho_II.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -11,129 +21,258 @@
 
 namespace {
 
+constexpr unsigned kFull = 0xffffffffu;
+
+// Per-bin counts; lanes holding the same bin combine into one atomic.
 __global__ void k_bin_count(const rb_candidate* __restrict__ cand, const unsigned long long* dev_count, int64_t cap,
                             int bin0, int nb, unsigned* __restrict__ count) {
   const int64_t n = (int64_t)min((unsigned long long)cap, *dev_count);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int b = cand[i].bin - bin0;
-    if (b >= 0 && b < nb) atomicAdd(count + b, 1u);
+  const int lane = threadIdx.x & 31;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~int64_t(31); i0 < n;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    int b = i < n ? cand[i].bin - bin0 : -1;
+    if (b >= nb) b = -1;
+    const unsigned peers = __match_any_sync(kFull, b);
+    if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(count + b, (unsigned)__popc(peers));
   }
 }
 
 // Exclusive scan of count[0, nb) into start[0, nb]; count is reset to zero (it becomes the
-// per-bin fill cursor). One CTA of 1024 threads, each owning a contiguous range of bins.
+// per-bin fill cursor). One CTA of 1024 threads walks the array in tiles of 8192 counters,
+// each thread scanning 8 consecutive ones, with a running carry between tiles.
 __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count, unsigned* __restrict__ start, int nb) {
   __shared__ unsigned wsum[32];
+  __shared__ unsigned carry_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int per = (nb + 1023) / 1024;
-  const int lo = min(nb, tid * per), hi = min(nb, lo + per);
-  unsigned s = 0;
-  for (int i = lo; i < hi; ++i) s += count[i];
-  unsigned inc = s;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
-    if (lane >= off) inc += y;
-  }
-  if (lane == 31) wsum[warp] = inc;
+  if (tid == 0) carry_s = 0;
   __syncthreads();
-  if (warp == 0) {
-    const unsigned v = wsum[lane];
-    unsigned x = v;
+  for (int base = 0; base < nb; base += 8192) {
+    unsigned v[8];
+    unsigned s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = base + tid * 8 + j;
+      v[j] = i < nb ? count[i] : 0u;
+      s += v[j];
+    }
+    unsigned inc = s;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
-      if (lane >= off) x += y;
+      const unsigned y = __shfl_up_sync(kFull, inc, off);
+      if (lane >= off) inc += y;
     }
-    wsum[lane] = x - v;
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned x0 = wsum[lane];
+      unsigned x = x0;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, x, off);
+        if (lane >= off) x += y;
+      }
+      wsum[lane] = x - x0;
+    }
+    __syncthreads();
+    const unsigned carry = carry_s;
+    unsigned run = carry + wsum[warp] + inc - s;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = base + tid * 8 + j;
+      if (i < nb) {
+        start[i] = run;
+        count[i] = 0;
+      }
+      run += v[j];
+    }
+    __syncthreads();
+    if (tid == 1023) carry_s = run;
+    __syncthreads();
   }
-  __syncthreads();
-  unsigned base = wsum[warp] + inc - s;
-  for (int i = lo; i < hi; ++i) {
-    start[i] = base;
-    base += count[i];
-    count[i] = 0;
-  }
-  if (tid == 1023) start[nb] = base;  // the last range ends at nb (possibly empty ranges before it)
+  if (tid == 0) start[nb] = carry_s;
 }
 
 __global__ void k_bin_scatter(const rb_candidate* __restrict__ cand, const unsigned long long* dev_count, int64_t cap,
                               int bin0, int nb, const unsigned* __restrict__ start, unsigned* __restrict__ cursor,
                               rb_candidate* __restrict__ out) {
   const int64_t n = (int64_t)min((unsigned long long)cap, *dev_count);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const rb_candidate c = cand[i];
-    const int b = c.bin - bin0;
-    if (b < 0 || b >= nb) continue;
-    out[start[b] + atomicAdd(cursor + b, 1u)] = c;
+  const int lane = threadIdx.x & 31;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~int64_t(31); i0 < n;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    rb_candidate c;
+    int b = -1;
+    if (i < n) {
+      c = cand[i];
+      b = c.bin - bin0;
+      if (b >= nb) b = -1;
+    }
+    const unsigned peers = __match_any_sync(kFull, b);
+    const int leader = __ffs(peers) - 1;
+    unsigned pos = 0;
+    if (b >= 0 && lane == leader) pos = atomicAdd(cursor + b, (unsigned)__popc(peers));
+    pos = __shfl_sync(kFull, pos, leader);
+    if (b >= 0) out[start[b] + pos + __popc(peers & ((1u << lane) - 1u))] = c;
   }
 }
 
+__device__ __forceinline__ uint32_t pack_h2(__half lo, __half hi) {
+  return (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+}
+// x -> (hi, lo) halves with hi + lo ~ x to about 22 bits
+__device__ __forceinline__ void split_h(float x, __half& h, __half& l) {
+  h = __float2half_rn(x);
+  l = __float2half_rn(x - __half2float(h));
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// W samples per bin -> NT = ceil(2W / 8) n-tiles of 8 columns (columns 2r, 2r+1 = Re, Im of sample r).
+template <int W>
+struct S2 {
+  static constexpr int NT = (2 * W + 7) / 8;
+};
+
+// Shared memory per bin: window [W][k16] float2, then fragments frag[plane][kc][nt][lane] (uint2).
 template <int W>
 __global__ void __launch_bounds__(256) k_stage2_bins(const float2* __restrict__ coeff, int ldk,
-                                                     const float2* __restrict__ beta, int k, int T, int64_t half,
-                                                     int bin0, int nb, const unsigned* __restrict__ start,
+                                                     const float2* __restrict__ beta, int k, int k16, int T,
+                                                     int64_t half, int bin0, int nb,
+                                                     const unsigned* __restrict__ start,
                                                      const rb_candidate* __restrict__ sorted, float thr2,
                                                      int64_t sample_offset, rb_trigger* __restrict__ trig,
                                                      unsigned long long* counter, int64_t cap) {
-  extern __shared__ float2 bs[];  // [W][k]: the bin's window of every basis series
+  constexpr int NT = S2<W>::NT;
+  extern __shared__ __align__(16) uint8_t s2mem[];
+  float2* win = reinterpret_cast<float2*>(s2mem);  // [W][k16]
+  const int nkc = 2 * k16 / 16;                     // K chunks: Re half then Im half
+  uint2* frag = reinterpret_cast<uint2*>(s2mem + sizeof(float2) * W * k16);  // [2][nkc][NT][32]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
   for (int b = blockIdx.x; b < nb; b += gridDim.x) {
     const unsigned c0 = start[b], c1 = start[b + 1];
     if (c0 == c1) continue;
     __syncthreads();
     const int64_t m0 = (int64_t)(bin0 + b) * W - half;
-    for (int idx = threadIdx.x; idx < k * W; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < k16 * W; idx += blockDim.x) {
       const int kk = idx / W, r = idx - kk * W;
-      bs[r * k + kk] = __ldg(beta + (int64_t)kk * half + m0 + r);
+      win[r * k16 + kk] = kk < k ? __ldg(beta + (int64_t)kk * half + m0 + r) : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    for (unsigned ci = c0 + warp; ci < c1; ci += nwarp) {
-      const rb_candidate cd = sorted[ci];
-      if (cd.tmpl < 0 || cd.tmpl >= T) continue;
-      float2 acc[W];
+    // B fragments: element (kk, n) for lane L: b0 = (kk = 16kc + 2t, +1), b1 = (+8, +9); n = 8 nt + g
+    for (int idx = threadIdx.x; idx < nkc * NT * 32; idx += blockDim.x) {
+      const int L = idx & 31, nt = (idx >> 5) % NT, kc = (idx >> 5) / NT;
+      const int gg = L >> 2, tt = L & 3;
+      const int n = nt * 8 + gg, r = n >> 1, part = n & 1;
+      __half hv[4], lv[4];
 #pragma unroll
-      for (int r = 0; r < W; ++r) acc[r] = make_float2(0.f, 0.f);
-      const float2* arow = coeff + (int64_t)cd.tmpl * ldk;
-      for (int kk = lane; kk < k; kk += 32) {
-        const float2 av = __ldg(arow + kk);
-#pragma unroll
-        for (int r = 0; r < W; ++r) {
-          const float2 bv = bs[r * k + kk];
-          acc[r].x = fmaf(av.x, bv.x, fmaf(av.y, bv.y, acc[r].x));
-          acc[r].y = fmaf(av.x, bv.y, fmaf(-av.y, bv.x, acc[r].y));
+      for (int e = 0; e < 4; ++e) {
+        const int kk = kc * 16 + 2 * tt + (e & 1) + (e >> 1) * 8;
+        float x = 0.f;
+        if (r < W) {
+          const bool im_half = kk >= k16;
+          const float2 bv = win[r * k16 + (im_half ? kk - k16 : kk)];
+          x = !im_half ? (part ? bv.y : bv.x) : (part ? -bv.x : bv.y);
         }
+        split_h(x, hv[e], lv[e]);
       }
+      frag[((0 * nkc + kc) * NT + nt) * 32 + L] = make_uint2(pack_h2(hv[0], hv[1]), pack_h2(hv[2], hv[3]));
+      frag[((1 * nkc + kc) * NT + nt) * 32 + L] = make_uint2(pack_h2(lv[0], lv[1]), pack_h2(lv[2], lv[3]));
+    }
+    __syncthreads();
+    for (unsigned base = c0 + warp * 16; base < c1; base += nwarp * 16) {
+      // rows g and g + 8 of the m16 tile are candidates base + g and base + g + 8
+      int tr[2];
 #pragma unroll
-      for (int r = 0; r < W; ++r)
+      for (int h = 0; h < 2; ++h) {
+        const unsigned ci = base + g + 8 * h;
+        const int t = ci < c1 ? sorted[ci].tmpl : -1;
+        tr[h] = (t >= 0 && t < T) ? t : -1;
+      }
+      float d[NT][4];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, off);
-          acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, off);
-        }
-      if (lane == 0) {
-        int best = 0;
-        float r2b = cabs2(acc[0]);
-        float2 zb = acc[0];
+      for (int nt = 0; nt < NT; ++nt) d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.f;
+      for (int c = 0; c < k16 / 16; ++c) {
+        // coefficients a[16c + 2t + {0, 1, 8, 9}] of the two rows, FP32 -> hi/lo halves
+        float2 av[2][4];
 #pragma unroll
-        for (int r = 1; r < W; ++r) {
-          const float r2 = cabs2(acc[r]);
-          if (r2 > r2b) {
-            r2b = r2;
-            best = r;
-            zb = acc[r];
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int kk = c * 16 + 2 * t4 + (e & 1) + (e >> 1) * 8;
+            av[h][e] = (tr[h] >= 0 && kk < k) ? __ldg(coeff + (int64_t)tr[h] * ldk + kk) : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {  // Re half (chunk c), then Im half (chunk k16/16 + c)
+          __half hh[2][4], ll[2][4];
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) split_h(part ? av[h][e].y : av[h][e].x, hh[h][e], ll[h][e]);
+          const uint32_t ah0 = pack_h2(hh[0][0], hh[0][1]), ah1 = pack_h2(hh[1][0], hh[1][1]);
+          const uint32_t ah2 = pack_h2(hh[0][2], hh[0][3]), ah3 = pack_h2(hh[1][2], hh[1][3]);
+          const uint32_t al0 = pack_h2(ll[0][0], ll[0][1]), al1 = pack_h2(ll[1][0], ll[1][1]);
+          const uint32_t al2 = pack_h2(ll[0][2], ll[0][3]), al3 = pack_h2(ll[1][2], ll[1][3]);
+          const int kc = part * (k16 / 16) + c;
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            const uint2 bh = frag[((0 * nkc + kc) * NT + nt) * 32 + lane];
+            const uint2 bl = frag[((1 * nkc + kc) * NT + nt) * 32 + lane];
+            mma16816(d[nt], ah0, ah1, ah2, ah3, bh.x, bh.y);
+            mma16816(d[nt], ah0, ah1, ah2, ah3, bl.x, bl.y);
+            mma16816(d[nt], al0, al1, al2, al3, bh.x, bh.y);
           }
         }
-        if (r2b >= thr2) {
+      }
+      // thread (g, t) holds, per n-tile, (Re, Im) of sample r = 4 nt + t for rows g and g + 8
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float best = -1.f, zr = 0.f, zi = 0.f;
+        int br = 0;
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const int r = 4 * nt + t4;
+          const float re = d[nt][2 * h], im = d[nt][2 * h + 1];
+          const float p2 = fmaf(re, re, im * im);
+          if (r < W && p2 > best) {
+            best = p2;
+            br = r;
+            zr = re;
+            zi = im;
+          }
+        }
+#pragma unroll
+        for (int off = 1; off < 4; off <<= 1) {
+          const float ob = __shfl_xor_sync(kFull, best, off);
+          const int orr = __shfl_xor_sync(kFull, br, off);
+          const float ozr = __shfl_xor_sync(kFull, zr, off);
+          const float ozi = __shfl_xor_sync(kFull, zi, off);
+          if (ob > best || (ob == best && orr < br)) {
+            best = ob;
+            br = orr;
+            zr = ozr;
+            zi = ozi;
+          }
+        }
+        if (t4 == 0 && tr[h] >= 0 && best >= thr2) {
+          const rb_candidate cd = sorted[base + g + 8 * h];
           const unsigned long long idx = atomicAdd(counter, 1ull);
           if ((int64_t)idx < cap) {
-            rb_trigger t;
-            t.sample = sample_offset + (int64_t)cd.bin * W + best;
-            t.tmpl = cd.tmpl;
-            t.block = cd.block;
-            t.snr = sqrtf(r2b);
-            t.phase = atan2f(zb.y, zb.x);
-            trig[idx] = t;
+            rb_trigger tg;
+            tg.sample = sample_offset + (int64_t)cd.bin * W + br;
+            tg.tmpl = cd.tmpl;
+            tg.block = cd.block;
+            tg.snr = sqrtf(best);
+            tg.phase = atan2f(zi, zr);
+            trig[idx] = tg;
           }
         }
       }
@@ -143,15 +282,22 @@ __global__ void __launch_bounds__(256) k_stage2_bins(const float2* __restrict__ 
 
 template <int W>
 int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
-                rb_trigger* trig, int64_t cap, cudaStream_t st) {
+                const float2* beta, rb_trigger* trig, int64_t cap, cudaStream_t st) {
+  constexpr int NT = S2<W>::NT;
   const int nb = (int)g.n_bins;
-  const int smem = W * d.k * (int)sizeof(float2);
+  const int k16 = (d.k + 15) / 16 * 16;
+  const int nkc = 2 * k16 / 16;
+  const int smem = (int)(sizeof(float2) * W * k16 + sizeof(uint2) * 2 * nkc * NT * 32);
+  if (smem > 200 * 1024) {
+    rb::set_detail("k * w too large for the second-stage window (%d x %d)", d.k, W);
+    return RB_ERR_UNSUPPORTED;
+  }
   auto kern = k_stage2_bins<W>;
   if (smem > 48 * 1024) RB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  const int grid = std::min(nb, 152 * 16);
-  kern<<<grid, 256, smem, st>>>(reinterpret_cast<const float2*>(b.coeff), b.k, ws.beta, d.k, d.n_templates, g.n / 2,
-                                nb, nb, ws.bin_start, ws.cand_sorted, d.rho_ii * d.rho_ii, d.sample_offset, trig,
-                                ws.trig_count, cap);
+  const int grid = std::min(nb, 152 * 8);
+  kern<<<grid, 256, smem, st>>>(reinterpret_cast<const float2*>(b.coeff), b.k, beta, d.k, k16, d.n_templates,
+                                g.n / 2, nb, nb, ws.bin_start, ws.cand_sorted, d.rho_ii * d.rho_ii, d.sample_offset,
+                                trig, ws.trig_count, cap);
   RB_LAUNCH_CHECK();
   return RB_OK;
 }
@@ -161,13 +307,9 @@ int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& 
 namespace rb {
 
 int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-                    rb_trigger* trig, int64_t cap, cudaStream_t st) {
+                    const float2* beta, rb_trigger* trig, int64_t cap, cudaStream_t st) {
   const int nb = (int)g.n_bins;
   const int bin0 = nb;  // valid bins are [n/(2w), n/w)
-  if (d.k * d.w * (int)sizeof(float2) > 200 * 1024) {
-    set_detail("k * w too large for the second-stage window (%d x %d)", d.k, d.w);
-    return RB_ERR_UNSUPPORTED;
-  }
   RB_CUDA_TRY(cudaMemsetAsync(ws.bin_count, 0, sizeof(unsigned) * (nb + 1), st));
   k_bin_count<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, nb, ws.bin_count);
   RB_LAUNCH_CHECK();
@@ -177,11 +319,11 @@ int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& 
                                          ws.bin_count, ws.cand_sorted);
   RB_LAUNCH_CHECK();
   switch (d.w) {
-    case 1: return launch_bins<1>(d, b, g, ws, trig, cap, st);
-    case 2: return launch_bins<2>(d, b, g, ws, trig, cap, st);
-    case 4: return launch_bins<4>(d, b, g, ws, trig, cap, st);
-    case 8: return launch_bins<8>(d, b, g, ws, trig, cap, st);
-    case 16: return launch_bins<16>(d, b, g, ws, trig, cap, st);
+    case 1: return launch_bins<1>(d, b, g, ws, beta, trig, cap, st);
+    case 2: return launch_bins<2>(d, b, g, ws, beta, trig, cap, st);
+    case 4: return launch_bins<4>(d, b, g, ws, beta, trig, cap, st);
+    case 8: return launch_bins<8>(d, b, g, ws, beta, trig, cap, st);
+    case 16: return launch_bins<16>(d, b, g, ws, beta, trig, cap, st);
   }
   return RB_ERR_BAD_INPUT;
 }
