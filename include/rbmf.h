@@ -212,6 +212,29 @@ int rb_filter_plain(const rb_filter_desc* desc, const float* templates, const fl
                     const double* psd, rb_trigger* trig, int64_t capacity, int64_t* n_trig,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * rb_filter_static - rb_filter without any device allocation, for callers that cannot allocate
+ * device memory: code running inside a host application that owns the whole GPU memory pool,
+ * latency-critical loops where an allocation may block or fail under memory pressure, and
+ * plugins whose host forbids allocation calls. (The paper has no counterpart; this is a
+ * deployment convenience.)
+ *
+ * Same arguments, results and errors as rb_filter minus the workspace: the scratch lives in a
+ * static device array of RB_STATIC_SCRATCH_BYTES (32 MiB) inside the library, which every GPU that
+ * loads the library keeps until the process exits. Problems whose rb_filter_plan workspace exceeds
+ * that size are rejected with RB_ERR_UNSUPPORTED (e.g. n = 16384, k = 64, T = 64 fits; the
+ * 2^19-sample, k = 256 workload does not). The call itself allocates nothing (no cudaMalloc, no
+ * allocating library routine).
+ *   - The first call on each device looks up the array's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents (every value a call
+ *     reads is written or cleared by that call first). Calls that overlap on the GPU - from two
+ *     streams or two host threads at once - race on it: serialise them.
+ */
+#define RB_STATIC_SCRATCH_BYTES (32u << 20)
+int rb_filter_static(const rb_filter_desc* desc, const rb_basis* basis, const float* strain, const double* psd,
+                     rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* stream);
+
 /* Stages of rb_filter timed by the profiler (CUDA events recorded on the call's stream). */
 enum {
   RB_STAGE_SETUP = 0,   /* status reset, twiddle tables, whitening weights */

@@ -85,6 +85,7 @@ SIGNATURES = {
     "rb_stage2": (C.c_int, [_D, _B, _P, _P, C.c_int64, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_plain": (C.c_int, [_D, _P, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
+    "rb_filter_static": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P]),
     "rb_profile_start": (C.c_int, []),
     "rb_profile_stop": (C.c_int, [C.POINTER(C.c_double), _I64P]),
     "rb_kernel_launches": (C.c_uint64, []),
