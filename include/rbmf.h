@@ -311,6 +311,50 @@ int rb_build(const rb_bank_desc* bank, const double* psd, int32_t k, int32_t ove
              uint64_t seed, float* vectors, float* coeff, double* sigma2, double* sv, void* workspace,
              size_t workspace_bytes, void* stream);
 
+/* Candidate refinement (step a8; not in the paper, which stops at the triggers). */
+typedef struct rb_refine_desc {
+  double fs;          /* sample rate [Hz] */
+  int64_t n;          /* block length (power of two, 2^10..2^20) */
+  double f_low;       /* lower cutoff [Hz] */
+  int32_t pn_order;   /* 0, 2 or 3 (non-spinning TaylorF2 as in rb_bank_desc) */
+  int32_t steps;      /* gradient-ascent steps for rb_refine */
+  double alpha0;      /* initial step length in scaled coordinates (e.g. 1e-3) */
+  double alpha_max;   /* step length cap (e.g. 0.05) */
+} rb_refine_desc;
+
+/*
+ * For a candidate theta = (mc [M_sun], eta, t_c [s from block start], phi_c) the matched filter of
+ * Eq. (1) at the template's own coalescence time (Eq. 3-4 with t_0 inside Psi) is
+ *   Z(theta) = sum_j s_hat[j] conj(g_j(theta)),  g_j = sqrt(4 df / S_j) f_j^(-7/6) exp(-i Psi(f_j; theta)),
+ *   J(theta) = |Z|^2 / sigma^2,                  sigma^2 = sum_j |g_j|^2,
+ * over the support f_low <= f_j < f_isco(theta_start), 0 < j < n/2, frozen at the starting point (so
+ * sigma does not depend on theta). Psi is evaluated in FP64 and reduced modulo 2 pi before FP32
+ * sin/cos; sums are accumulated in FP64. One CTA per candidate; the template is recomputed in every
+ * pass, no per-template series is stored.
+ *   s_hat: [n/2] complex device (rb_whiten output).  psd: [n/2+1] float64 device.
+ *   theta: [n_cand][4] float64 device.  workspace: at least rb_refine_workspace_bytes(desc) bytes.
+ */
+size_t rb_refine_workspace_bytes(const rb_refine_desc* desc);
+
+/* rb_refine_eval - J [n_cand] and Z [n_cand] complex (float64 pairs) at theta (the forward pass). */
+int rb_refine_eval(const rb_refine_desc* desc, const float* s_hat, const double* psd, const double* theta,
+                   double* J, double* Z, int64_t n_cand, void* workspace, size_t workspace_bytes, void* stream);
+
+/* rb_refine_adjoint - the backward pass: given dL/dJ [n_cand] and the forward Z, recomputes the
+ * templates and returns dL/dtheta [n_cand][4] = dL/dJ * 2 Re(conj(Z) dZ/dtheta) / sigma^2 with
+ * dZ/dtheta = sum_j s_hat[j] (i dPsi_j/dtheta) conj(g_j). */
+int rb_refine_adjoint(const rb_refine_desc* desc, const float* s_hat, const double* psd, const double* theta,
+                      const double* Z, const double* dJ, double* dtheta, int64_t n_cand, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* rb_refine - desc->steps of normalised gradient ascent of J in scaled coordinates
+ * u = (mc/mc_start, eta, t_c * 100 Hz, phi_c): a step of length alpha along the normalised gradient is
+ * kept only if J increases (then alpha doubles, capped at alpha_max), otherwise alpha halves; eta is
+ * clamped to [0.05, 0.25]. theta is updated in place; J [n_cand] receives the final J.
+ * Errors: RB_ERR_BAD_INPUT (sizes, pn_order, eta outside (0, 0.25], mc <= 0). */
+int rb_refine(const rb_refine_desc* desc, const float* s_hat, const double* psd, double* theta, double* J,
+              int64_t n_cand, void* workspace, size_t workspace_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,7 +63,12 @@ class rb_bank_desc(C.Structure):
                 ("pn_order", C.c_int32), ("params", C.c_void_p)]
 
 
-EXTRA_STRUCTS = {"rb_bank_desc": rb_bank_desc}
+class rb_refine_desc(C.Structure):
+    _fields_ = [("fs", C.c_double), ("n", C.c_int64), ("f_low", C.c_double), ("pn_order", C.c_int32),
+                ("steps", C.c_int32), ("alpha0", C.c_double), ("alpha_max", C.c_double)]
+
+
+EXTRA_STRUCTS = {"rb_bank_desc": rb_bank_desc, "rb_refine_desc": rb_refine_desc}
 
 assert C.sizeof(rb_trigger) == 24 and C.sizeof(rb_candidate) == 16
 
@@ -86,6 +91,11 @@ SIGNATURES = {
     "rb_filter": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_plain": (C.c_int, [_D, _P, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_static": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P]),
+    "rb_refine_workspace_bytes": (C.c_size_t, [C.POINTER(rb_refine_desc)]),
+    "rb_refine_eval": (C.c_int, [C.POINTER(rb_refine_desc), _P, _P, _P, _P, _P, C.c_int64, _P, C.c_size_t, _P]),
+    "rb_refine_adjoint": (C.c_int, [C.POINTER(rb_refine_desc), _P, _P, _P, _P, _P, _P, C.c_int64, _P, C.c_size_t,
+                                    _P]),
+    "rb_refine": (C.c_int, [C.POINTER(rb_refine_desc), _P, _P, _P, _P, C.c_int64, _P, C.c_size_t, _P]),
     "rb_profile_start": (C.c_int, []),
     "rb_profile_stop": (C.c_int, [C.POINTER(C.c_double), _I64P]),
     "rb_kernel_launches": (C.c_uint64, []),

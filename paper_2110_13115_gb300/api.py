@@ -239,3 +239,70 @@ def rb_profile_stop():
 
 def rb_kernel_launches() -> int:
     return int(_lib().rb_kernel_launches())
+
+
+# --- candidate refinement (step a8) --------------------------------------------------------
+
+def make_refine_desc(fs, n, f_low, pn_order=2, steps=20, alpha0=1e-3, alpha_max=0.05) -> N.rb_refine_desc:
+    return N.rb_refine_desc(float(fs), int(n), float(f_low), int(pn_order), int(steps), float(alpha0),
+                            float(alpha_max))
+
+
+def _refine_ws(desc, device):
+    return torch.empty(int(_lib().rb_refine_workspace_bytes(C.byref(desc))), dtype=torch.uint8, device=device)
+
+
+def rb_refine_eval(desc, s_hat: torch.Tensor, psd: torch.Tensor, theta: torch.Tensor):
+    """J [n] and Z [n] complex128 at theta [n, 4] float64 (device)."""
+    theta = theta.contiguous()
+    n = theta.shape[0]
+    J = torch.empty(n, dtype=torch.float64, device=theta.device)
+    Z = torch.empty(n, dtype=torch.complex128, device=theta.device)
+    ws = _refine_ws(desc, theta.device)
+    rc = _lib().rb_refine_eval(C.byref(desc), _p(s_hat), _p(psd), _p(theta), _p(J), _p(Z), n, _p(ws), ws.numel(),
+                               _stream())
+    N.check("rb_refine_eval", rc)
+    return J, Z
+
+
+def rb_refine_adjoint(desc, s_hat, psd, theta, Z, dJ):
+    theta = theta.contiguous()
+    n = theta.shape[0]
+    dtheta = torch.empty((n, 4), dtype=torch.float64, device=theta.device)
+    ws = _refine_ws(desc, theta.device)
+    rc = _lib().rb_refine_adjoint(C.byref(desc), _p(s_hat), _p(psd), _p(theta), _p(Z.contiguous()),
+                                  _p(dJ.contiguous()), _p(dtheta), n, _p(ws), ws.numel(), _stream())
+    N.check("rb_refine_adjoint", rc)
+    return dtheta
+
+
+def rb_refine(desc, s_hat: torch.Tensor, psd: torch.Tensor, theta: torch.Tensor):
+    """desc.steps of gradient ascent; returns (refined theta [n, 4], J [n]) (device, new tensors)."""
+    th = theta.detach().clone().contiguous()
+    n = th.shape[0]
+    J = torch.empty(n, dtype=torch.float64, device=th.device)
+    ws = _refine_ws(desc, th.device)
+    rc = _lib().rb_refine(C.byref(desc), _p(s_hat), _p(psd), _p(th), _p(J), n, _p(ws), ws.numel(), _stream())
+    N.check("rb_refine", rc)
+    return th, J
+
+
+class PeakSNR2(torch.autograd.Function):
+    """J(theta) = |Z|^2 / sigma^2 per candidate; backward runs the adjoint kernel (templates recomputed)."""
+
+    @staticmethod
+    def forward(ctx, theta, s_hat, psd, desc):
+        J, Z = rb_refine_eval(desc, s_hat, psd, theta.detach())
+        ctx.save_for_backward(theta.detach(), Z)
+        ctx.s_hat, ctx.psd, ctx.desc = s_hat, psd, desc
+        return J
+
+    @staticmethod
+    def backward(ctx, gJ):
+        theta, Z = ctx.saved_tensors
+        dtheta = rb_refine_adjoint(ctx.desc, ctx.s_hat, ctx.psd, theta, Z, gJ.to(torch.float64))
+        return dtheta, None, None, None
+
+
+def peak_snr2(theta, s_hat, psd, desc):
+    return PeakSNR2.apply(theta, s_hat, psd, desc)

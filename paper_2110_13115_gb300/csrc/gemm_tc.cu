@@ -131,6 +131,20 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Grouped rasterisation: tiles run in groups of kGroupM row blocks x all column blocks, column
+// fastest within a group, so the ~152 tiles in flight share each B tile among kGroupM CTAs and
+// each A tile among ~152 / kGroupM CTAs instead of all of them hitting the same lines.
+constexpr int kGroupM = 8;
+__device__ __forceinline__ void tile_coords(int tile, int num_m, int num_n, int& mb, int& nb) {
+  const int per_group = kGroupM * num_n;
+  const int group = tile / per_group;
+  const int first_m = group * kGroupM;
+  const int rows = min(kGroupM, num_m - first_m);
+  const int local = tile - group * per_group;
+  mb = first_m + local % rows;
+  nb = local / rows;
+}
+
 template <int NPLANES, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     k_stage1_tc(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
@@ -181,7 +195,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int used = 0;  // stages that received at least one load
       for (int tile = blockIdx.x; tile < num_tiles && !abort_flag; tile += gridDim.x) {
-        const int mb = tile % p.num_m, nb = tile / p.num_m;
+        int mb, nb;
+        tile_coords(tile, p.num_m, p.num_n, mb, nb);
         for (int kb = 0; kb < p.KB; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1, &abort_flag)) {
             fail();
@@ -282,7 +297,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc_fence_after();
-      const int mb = tile % p.num_m, nb = tile / p.num_m;
+      int mb, nb;
+      tile_coords(tile, p.num_m, p.num_n, mb, nb);
       const int row = mb * BM + q * 32 + lane;
       const int t = row >> 1;
       const bool even = (lane & 1) == 0;
