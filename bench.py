@@ -310,9 +310,16 @@ def main():
 
     d = api.make_desc(g.fs, g.n, args.k, T, w=args.w, precision=args.precision, rho_i=rho_i, rho_ii=wl.rho_ii,
                       cand_capacity=1 << 25, sample_offset=0, block_id=rank)
+    ws = api.workspace(d)
+    tuned = None
     if args.precision != "fp32":
         api.rb_pack_coeff(d, basis)
-    ws = api.workspace(d)
+        # autotune the first stage's tile variant on this block's operands (setup, untimed)
+        sh = api.rb_whiten(d, strain_d, psd_d, ws=ws)
+        _, bavg_t = api.rb_basis_filter(d, basis, sh, keep_beta=False, ws=ws)
+        chosen, times = api.rb_tune_stage1(d, basis, bavg_t, ws=ws)
+        tuned = dict(variant=chosen, n_tile=[256, 128][chosen], ms_by_variant=times)
+        del sh, bavg_t
     cap = 1 << 23
     trig = torch.empty(cap * 24, dtype=torch.uint8, device="cuda")
 
@@ -443,6 +450,7 @@ def main():
                            k=args.k, w=args.w, rho_I=rho_i, rho_II=wl.rho_ii, first_stage=args.precision,
                            rho_I_calibration=f"noise-only block, {n_cal} flat triggers, recovery {args.recovery}",
                            l2="inputs larger than L2: the basis alone is 537 MB per step",
+                           first_stage_tile=tuned,
                            parallelism=f"replicas x{world} (one block per GPU)"),
                roofline=roof, cpu_baseline=cpu,
                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h_total // args.steps),

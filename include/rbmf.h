@@ -235,6 +235,22 @@ int rb_filter_plain(const rb_filter_desc* desc, const float* templates, const fl
 int rb_filter_static(const rb_filter_desc* desc, const rb_basis* basis, const float* strain, const double* psd,
                      rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* stream);
 
+/*
+ * rb_tune_stage1 - autotuner of the tensor-core first stage: packs beta_avg (as rb_stage1 does), times
+ * each tile variant of the tcgen05 kernel (N-tile width 256 or 128 columns with the deepest operand
+ * ring that fits in shared memory) with the threshold disabled, and remembers the fastest for this
+ * (precision, T, n_bins, kp) in a process-wide table that rb_stage1 / rb_filter consult (variant 0
+ * when untuned). Measurement support, not in the paper.
+ *   beta_avg: [k][n/(2w)] complex device.  times_ms: HOST [RB_STAGE1_VARIANTS] mean ms per launch.
+ *   chosen: HOST, the selected variant. Synchronises `stream`.
+ */
+#define RB_STAGE1_VARIANTS 2
+/* rb_set_stage1_variant - pin the tile variant (0: N-tile 256, 1: N-tile 128) used for desc's shape
+ * and precision, overriding the tuner's choice. Host only. Errors: RB_ERR_BAD_INPUT. */
+int rb_set_stage1_variant(const rb_filter_desc* desc, int32_t variant);
+int rb_tune_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* beta_avg, double* times_ms,
+                   int32_t* chosen, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Stages of rb_filter timed by the profiler (CUDA events recorded on the call's stream). */
 enum {
   RB_STAGE_SETUP = 0,   /* status reset, twiddle tables, whitening weights */

@@ -91,6 +91,8 @@ SIGNATURES = {
     "rb_filter": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_plain": (C.c_int, [_D, _P, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_static": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P]),
+    "rb_set_stage1_variant": (C.c_int, [_D, C.c_int32]),
+    "rb_tune_stage1": (C.c_int, [_D, _B, _P, C.POINTER(C.c_double), C.POINTER(C.c_int32), _P, C.c_size_t, _P]),
     "rb_refine_workspace_bytes": (C.c_size_t, [C.POINTER(rb_refine_desc)]),
     "rb_refine_eval": (C.c_int, [C.POINTER(rb_refine_desc), _P, _P, _P, _P, _P, C.c_int64, _P, C.c_size_t, _P]),
     "rb_refine_adjoint": (C.c_int, [C.POINTER(rb_refine_desc), _P, _P, _P, _P, _P, _P, C.c_int64, _P, C.c_size_t,

@@ -306,3 +306,19 @@ class PeakSNR2(torch.autograd.Function):
 
 def peak_snr2(theta, s_hat, psd, desc):
     return PeakSNR2.apply(theta, s_hat, psd, desc)
+
+
+def rb_tune_stage1(desc, basis: Basis, beta_avg: torch.Tensor, ws=None):
+    """Time the first-stage tile variants on these operands; returns (chosen variant, times in ms)."""
+    ws = workspace(desc) if ws is None else ws
+    times = (C.c_double * 2)()
+    chosen = C.c_int32(0)
+    b = basis.c_struct()
+    rc = _lib().rb_tune_stage1(C.byref(desc), C.byref(b), _p(beta_avg), times, C.byref(chosen), _p(ws), ws.numel(),
+                               _stream())
+    N.check("rb_tune_stage1", rc)
+    return chosen.value, list(times)
+
+
+def rb_set_stage1_variant(desc, variant: int):
+    N.check("rb_set_stage1_variant", _lib().rb_set_stage1_variant(C.byref(desc), int(variant)))

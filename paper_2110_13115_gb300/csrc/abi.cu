@@ -372,6 +372,41 @@ int rb_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* be
   return (int64_t)s.cand > desc->cand_capacity ? RB_ERR_OVERFLOW : RB_OK;
 }
 
+int rb_set_stage1_variant(const rb_filter_desc* desc, int32_t variant) {
+  if (!desc) {
+    set_detail("desc is NULL");
+    return RB_ERR_BAD_INPUT;
+  }
+  Geometry g;
+  int rc = make_geometry(*desc, &g);
+  if (rc) return rc;
+  return set_stage1_variant(*desc, g, variant);
+}
+
+int rb_tune_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* beta_avg, double* times_ms,
+                   int32_t* chosen, void* workspace, size_t workspace_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Geometry g;
+  Workspace ws;
+  int rc = prepare(desc, workspace, workspace_bytes, false, &g, &ws, st);
+  if (rc) return rc;
+  if ((rc = check_basis(*desc, basis))) return rc;
+  if (desc->precision == RB_PREC_FP32 || !basis->coeff_op || basis->coeff_op_precision != desc->precision) {
+    set_detail("tuning needs a 16-bit precision with a matching packed coeff_op");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (!beta_avg || !times_ms || !chosen) {
+    set_detail("NULL argument");
+    return RB_ERR_BAD_INPUT;
+  }
+  if ((rc = pack_beta(*desc, g, (const float2*)beta_avg, ws.bop_hi, ws.bop_lo, st))) return rc;
+  for (int v = 0; v < RB_STAGE1_VARIANTS; ++v) times_ms[v] = -1.0;
+  int best = 0;
+  if ((rc = tune_stage1(*desc, *basis, g, ws, times_ms, &best, st))) return rc;
+  *chosen = best;
+  return RB_OK;
+}
+
 int rb_stage2(const rb_filter_desc* desc, const rb_basis* basis, const float* beta, const rb_candidate* cand,
               int64_t n_cand, rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* workspace,
               size_t workspace_bytes, void* stream) {

@@ -10,9 +10,9 @@
 //
 // Persistent kernel, one CTA per SM, 320 threads:
 //   warp 0  : TMA producer (one thread) - 128B-swizzled K-major tiles of A (128 x 64) and
-//             B (256 x 64) per plane into a STAGES-deep shared-memory ring;
-//   warp 1  : tensor-memory allocation (512 columns) and the MMA issuer (one thread),
-//             M = 128, N = 256, K = 16 per instruction, two accumulator buffers;
+//             B (BN x 64) per plane into a STAGES-deep shared-memory ring;
+//   warp 1  : tensor-memory allocation (2 BN columns) and the MMA issuer (one thread),
+//             M = 128, N = BN, K = 16 per instruction, two accumulator buffers;
 //   warps 2-9: epilogue, two per 32-lane quarter of tensor memory (half the columns each).
 // Every mbarrier wait is bounded (1 s of %globaltimer); a timeout sets RB_FLAG_TIMEOUT, makes the
 // other roles stop, waits (bounded) for the copies and products in flight, frees tensor memory
@@ -22,16 +22,18 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 #include "internal.h"
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int BM = 128, BK = 64;
 constexpr int kThreads = 320;  // producer warp, MMA warp, 8 epilogue warps
-constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitNs = 1000000000ull;
 
 struct TcParams {
@@ -131,21 +133,14 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Grouped rasterisation: tiles run in groups of kGroupM row blocks x all column blocks, column
-// fastest within a group, so the ~152 tiles in flight share each B tile among kGroupM CTAs and
-// each A tile among ~152 / kGroupM CTAs instead of all of them hitting the same lines.
-constexpr int kGroupM = 8;
+// Tile order: row blocks fastest, so the tiles in flight share one B tile (it is read from L2 by
+// every CTA while all of A stays L2-resident). Grouping rows x columns measured slower.
 __device__ __forceinline__ void tile_coords(int tile, int num_m, int num_n, int& mb, int& nb) {
-  const int per_group = kGroupM * num_n;
-  const int group = tile / per_group;
-  const int first_m = group * kGroupM;
-  const int rows = min(kGroupM, num_m - first_m);
-  const int local = tile - group * per_group;
-  mb = first_m + local % rows;
-  nb = local / rows;
+  mb = tile % num_m;
+  nb = tile / num_m;
 }
 
-template <int NPLANES, int STAGES>
+template <int NPLANES, int STAGES, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_stage1_tc(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                 const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1, TcParams p) {
@@ -175,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
-                 "r"(kTmemCols)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -290,7 +285,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     int acc = 0;
     uint32_t acc_phase = 0;
     const unsigned full_mask = 0xffffffffu;
-    const unsigned lt_mask = (1u << lane) - 1u;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
       if (!mbar_wait(&tfull[acc], acc_phase, &abort_flag)) {
         if (lane == 0) fail();
@@ -317,28 +311,35 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const int col0 = nb * BN + c0;
         if (!__any_sync(full_mask, trow && col0 < p.N && pmax >= p.thr2)) continue;
+        // one counter reservation per warp and chunk: per-lane hit masks, a warp scan of the
+        // counts, then each lane writes its hits in column order
+        unsigned hits = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          hits |= (unsigned)(trow && col0 + j < p.N && v[j] >= p.thr2) << j;
+        const int cnt = __popc(hits);
+        int incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int y = __shfl_up_sync(full_mask, incl, off);
+          if (lane >= off) incl += y;
+        }
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(p.counter, (unsigned long long)incl);
+        base = __shfl_sync(full_mask, base, 31);
+        unsigned long long idx = base + (unsigned long long)(incl - cnt);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const float p2 = v[j];
-          const int col = col0 + j;
-          const bool hit = trow && col < p.N && p2 >= p.thr2;
-          const unsigned mask = __ballot_sync(full_mask, hit);
-          if (mask) {
-            const int leader = __ffs(mask) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(p.counter, (unsigned long long)__popc(mask));
-            base = __shfl_sync(full_mask, base, leader);
-            if (hit) {
-              const unsigned long long idx = base + __popc(mask & lt_mask);
-              if ((long long)idx < p.cap) {
-                rb_candidate c;
-                c.tmpl = t;
-                c.bin = p.bin0 + col;
-                c.snr_avg = sqrtf(p2);
-                c.block = p.block_id;
-                p.cand[idx] = c;
-              }
+          if ((hits >> j) & 1u) {
+            if ((long long)idx < p.cap) {
+              rb_candidate c;
+              c.tmpl = t;
+              c.bin = p.bin0 + col0 + j;
+              c.snr_avg = sqrtf(v[j]);
+              c.block = p.block_id;
+              p.cand[idx] = c;
             }
+            ++idx;
           }
         }
       }
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
   }
 }
 
@@ -404,10 +405,11 @@ int make_map(CUtensorMap* m, const void* base, bool bf16, int64_t kp, int64_t ro
   return RB_OK;
 }
 
-template <int NPLANES, int STAGES>
+template <int NPLANES, int STAGES, int BN>
 int launch_tc(const CUtensorMap* maps, const TcParams& p, cudaStream_t st) {
   constexpr int smem = STAGES * NPLANES * (BM * BK * 2 + BN * BK * 2) + 1024;
-  auto kern = k_stage1_tc<NPLANES, STAGES>;
+  static_assert(smem <= 227 * 1024, "shared memory budget");
+  auto kern = k_stage1_tc<NPLANES, STAGES, BN>;
   RB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int dev = 0, sms = 0;
   RB_CUDA_TRY(cudaGetDevice(&dev));
@@ -419,16 +421,38 @@ int launch_tc(const CUtensorMap* maps, const TcParams& p, cudaStream_t st) {
   return RB_OK;
 }
 
-}  // namespace
+// Tile variants (the autotuner's search space): N-tile width and the ring depth that fits.
+constexpr int kVariants = 2;
+constexpr int kVariantBN[kVariants] = {256, 128};
 
-namespace rb {
+int launch_variant(int v, bool split, const CUtensorMap* maps, const TcParams& p, cudaStream_t st) {
+  if (v == 0) return split ? launch_tc<2, 2, 256>(maps, p, st) : launch_tc<1, 4, 256>(maps, p, st);
+  return split ? launch_tc<2, 3, 128>(maps, p, st) : launch_tc<1, 6, 128>(maps, p, st);
+}
 
-int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws, rb_candidate* cand,
-              cudaStream_t st) {
+struct TuneKey {
+  int precision, T;
+  int64_t n_bins;
+  int kp;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(precision, T, n_bins, kp) < std::tie(o.precision, o.T, o.n_bins, o.kp);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+int chosen_variant(const rb_filter_desc& d, const rb::Geometry& g) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(TuneKey{d.precision, d.n_templates, g.n_bins, g.kp});
+  return it == g_tuned.end() ? 0 : it->second;
+}
+
+int build_params(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
+                 rb_candidate* cand, int variant, CUtensorMap* maps, TcParams& p) {
+  const int BN = kVariantBN[variant];
   const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
   const bool bf = d.precision == RB_PREC_BF16 || d.precision == RB_PREC_BF16_SPLIT;
   const int64_t M = 2 * (int64_t)d.n_templates;
-  CUtensorMap maps[4];
   const uint16_t* a0 = (const uint16_t*)b.coeff_op;
   const uint16_t* a1 = split ? a0 + M * g.kp : a0;
   int rc;
@@ -436,7 +460,6 @@ int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, con
   if ((rc = make_map(&maps[1], a1, bf, g.kp, M, BM))) return rc;
   if ((rc = make_map(&maps[2], ws.bop_hi, bf, g.kp, g.n_bins, BN))) return rc;
   if ((rc = make_map(&maps[3], split ? ws.bop_lo : ws.bop_hi, bf, g.kp, g.n_bins, BN))) return rc;
-  TcParams p;
   p.T = d.n_templates;
   p.N = (int)g.n_bins;
   p.KB = g.kp / BK;
@@ -451,7 +474,77 @@ int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, con
   p.flags = ws.flags;
   const uint32_t fmt = bf ? 1u : 0u;
   p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-  return split ? launch_tc<2, 2>(maps, p, st) : launch_tc<1, 4>(maps, p, st);
+  return RB_OK;
+}
+
+}  // namespace
+
+namespace rb {
+
+int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws, rb_candidate* cand,
+              cudaStream_t st) {
+  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
+  const int v = chosen_variant(d, g);
+  CUtensorMap maps[4];
+  TcParams p;
+  int rc = build_params(d, b, g, ws, cand, v, maps, p);
+  if (rc) return rc;
+  return launch_variant(v, split, maps, p, st);
+}
+
+// Time every variant on the packed operands in the workspace (threshold disabled so no candidate is
+// written), remember the fastest for this shape and precision, and report the times.
+int tune_stage1(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws, double* ms,
+                int* chosen, cudaStream_t st) {
+  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
+  cudaEvent_t e0, e1;
+  RB_CUDA_TRY(cudaEventCreate(&e0));
+  RB_CUDA_TRY(cudaEventCreate(&e1));
+  int best = 0, rc = RB_OK;
+  double best_ms = 1e30;
+  for (int v = 0; v < kVariants && rc == RB_OK; ++v) {
+    CUtensorMap maps[4];
+    TcParams p;
+    if ((rc = build_params(d, b, g, ws, ws.cand, v, maps, p))) break;
+    p.thr2 = INFINITY;
+    if ((rc = launch_variant(v, split, maps, p, st))) break;  // warm-up
+    const int reps = 3;
+    if (cudaEventRecord(e0, st) != cudaSuccess) rc = RB_ERR_CUDA;
+    for (int r = 0; r < reps && rc == RB_OK; ++r) rc = launch_variant(v, split, maps, p, st);
+    if (rc) break;
+    float t = 0.f;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+      rc = RB_ERR_CUDA;
+      break;
+    }
+    ms[v] = t / reps;
+    if (ms[v] < best_ms) {
+      best_ms = ms[v];
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[TuneKey{d.precision, d.n_templates, g.n_bins, g.kp}] = best;
+  }
+  *chosen = best;
+  return RB_OK;
+}
+
+int stage1_tc_variants() { return kVariants; }
+
+int set_stage1_variant(const rb_filter_desc& d, const Geometry& g, int variant) {
+  if (variant < 0 || variant >= kVariants) {
+    set_detail("variant %d out of range", variant);
+    return RB_ERR_BAD_INPUT;
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned[TuneKey{d.precision, d.n_templates, g.n_bins, g.kp}] = variant;
+  return RB_OK;
 }
 
 }  // namespace rb

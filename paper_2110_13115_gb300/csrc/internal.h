@@ -67,6 +67,10 @@ int pack_beta(const rb_filter_desc& d, const Geometry& g, const float2* bavg, vo
 int pack_coeff(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, void* out, cudaStream_t st);
 int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
               rb_candidate* cand, cudaStream_t st);
+int tune_stage1(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws, double* ms,
+                int* chosen, cudaStream_t st);
+int stage1_tc_variants();
+int set_stage1_variant(const rb_filter_desc& d, const Geometry& g, int variant);
 int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
                     const float2* beta, rb_trigger* trig, int64_t cap, cudaStream_t st);
 

@@ -262,9 +262,17 @@ __global__ void __launch_bounds__(256) k_stage2_bins(const float2* __restrict__ 
             zi = ozi;
           }
         }
-        if (t4 == 0 && tr[h] >= 0 && best >= thr2) {
+        // one counter reservation per warp for its (up to 8) triggers of this half
+        const bool emit = t4 == 0 && tr[h] >= 0 && best >= thr2;
+        const unsigned em = __ballot_sync(kFull, emit);
+        if (!em) continue;
+        const int leader = __ffs(em) - 1;
+        unsigned long long b0 = 0;
+        if (lane == leader) b0 = atomicAdd(counter, (unsigned long long)__popc(em));
+        b0 = __shfl_sync(kFull, b0, leader);
+        if (emit) {
           const rb_candidate cd = sorted[base + g + 8 * h];
-          const unsigned long long idx = atomicAdd(counter, 1ull);
+          const unsigned long long idx = b0 + __popc(em & ((1u << lane) - 1u));
           if ((int64_t)idx < cap) {
             rb_trigger tg;
             tg.sample = sample_offset + (int64_t)cd.bin * W + br;

@@ -25,7 +25,7 @@ def api():
     return A
 
 
-def _case(api, T, k, n, w, rho_i, prec, seed=1):
+def _case(api, T, k, n, w, rho_i, prec, seed=1, variant=0):
     nb = n // (2 * w)
     a = inputs.complex_normal((T, k), seed)
     a = (a / np.linalg.norm(a, axis=1, keepdims=True)).astype(np.complex64)
@@ -33,6 +33,7 @@ def _case(api, T, k, n, w, rho_i, prec, seed=1):
     d = api.make_desc(1024.0, n, k, T, w=w, precision=prec, rho_i=rho_i, cand_capacity=1 << 22)
     basis = api.Basis(torch.zeros((k, n // 2), dtype=torch.complex64, device="cuda"), torch.from_numpy(a).cuda(), n)
     api.rb_pack_coeff(d, basis)
+    api.rb_set_stage1_variant(d, variant)
     buf, nc = api.rb_stage1(d, basis, torch.from_numpy(bv).cuda())
     got = api.candidates_numpy(buf, nc)
     full = np.zeros((k, n // w), np.complex128)
@@ -41,14 +42,15 @@ def _case(api, T, k, n, w, rho_i, prec, seed=1):
     return got, ref, r, nb
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("prec", ["fp16_split", "bf16_split", "fp16", "bf16"])
 @pytest.mark.parametrize("T,k,n,w", [(64, 32, 1 << 14, 16),  # one M tile, two N tiles, K = 64
                                      (200, 24, 1 << 14, 8),  # ragged M (400 rows), ragged K (48 -> 64)
                                      (333, 96, 1 << 15, 4),  # ragged M, N = 4096, K = 192
                                      (1000, 256, 1 << 16, 16)])  # K = 512 (eight K blocks)
-def test_stage1_tc_parity(api, prec, T, k, n, w):
+def test_stage1_tc_parity(api, prec, T, k, n, w, variant):
     rho_i = 2.6
-    got, ref, r, nb = _case(api, T, k, n, w, rho_i, prec)
+    got, ref, r, nb = _case(api, T, k, n, w, rho_i, prec, variant=variant)
     band = max(REL[prec] * 2, 1e-3)
     gset = set(zip(got["tmpl"].tolist(), got["bin"].tolist()))
     oset = set(zip(ref["template"].tolist(), ref["bin"].tolist()))
@@ -61,10 +63,11 @@ def test_stage1_tc_parity(api, prec, T, k, n, w):
     assert max(errs) < REL[prec], (prec, max(errs))
 
 
-def test_stage1_tc_everything_passes_at_zero_threshold(api):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_stage1_tc_everything_passes_at_zero_threshold(api, variant):
     """rho_I = 0 keeps every (template, valid bin): exact count, padding rows and columns excluded."""
     T, k, n, w = 70, 40, 1 << 13, 8
-    got, ref, r, nb = _case(api, T, k, n, w, 0.0, "fp16_split")
+    got, ref, r, nb = _case(api, T, k, n, w, 0.0, "fp16_split", variant=variant)
     assert len(got) == T * nb == len(ref)
     assert got["bin"].min() == nb and got["bin"].max() == 2 * nb - 1
     assert got["tmpl"].max() == T - 1
@@ -111,3 +114,25 @@ def test_pipeline_tc_real_bank_vs_oracle_rb(api, prec, w, rho_i):
     band = max(2 * REL[prec], 1e-3)
     stats = compare_triggers(got, ref, w, rho_ii, ref_rho=zfull, rho_avg=ravg, rho_i=rho_i, band=band)
     assert stats["both"] >= 3, stats
+
+
+def test_tuner_picks_a_variant(api):
+    T, k, n, w = 500, 64, 1 << 15, 8
+    nb = n // (2 * w)
+    a = inputs.complex_normal((T, k), 5)
+    a = (a / np.linalg.norm(a, axis=1, keepdims=True)).astype(np.complex64)
+    bv = inputs.complex_normal((k, nb), 6).astype(np.complex64)
+    d = api.make_desc(1024.0, n, k, T, w=w, precision="fp16", rho_i=3.0, cand_capacity=1 << 20)
+    basis = api.Basis(torch.zeros((k, n // 2), dtype=torch.complex64, device="cuda"), torch.from_numpy(a).cuda(), n)
+    api.rb_pack_coeff(d, basis)
+    chosen, times = api.rb_tune_stage1(d, basis, torch.from_numpy(bv).cuda())
+    assert chosen in (0, 1) and all(t > 0 for t in times)
+    assert times[chosen] == min(times)
+    # the tuned choice is used afterwards and still gives the oracle's candidates
+    buf, nc = api.rb_stage1(d, basis, torch.from_numpy(bv).cuda())
+    full = np.zeros((k, n // w), np.complex128)
+    full[:, nb:] = bv
+    ref, r = rb.stage1(a.astype(np.complex128), full, n, w, 3.0)
+    got = api.candidates_numpy(buf, nc)
+    diff = set(zip(got["tmpl"].tolist(), got["bin"].tolist())) ^ set(zip(ref["template"].tolist(), ref["bin"].tolist()))
+    assert all(abs(r[t, i - nb] - 3.0) <= 6e-3 * 3.0 for t, i in diff)
