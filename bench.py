@@ -312,8 +312,8 @@ def main():
                       cand_capacity=1 << 25, sample_offset=0, block_id=rank)
     ws = api.workspace(d)
     tuned = None
+    api.rb_pack_coeff(d, basis)
     if args.precision != "fp32":
-        api.rb_pack_coeff(d, basis)
         # autotune the first stage's tile variant on this block's operands (setup, untimed)
         sh = api.rb_whiten(d, strain_d, psd_d, ws=ws)
         _, bavg_t = api.rb_basis_filter(d, basis, sh, keep_beta=False, ws=ws)

@@ -63,7 +63,7 @@ typedef struct rb_filter_desc {
   int32_t precision;      /* RB_PREC_* for the first stage */
   float rho_i;            /* first-stage threshold on the bin-averaged SNR (Sec. III.C) */
   float rho_ii;           /* second-stage threshold on the full-rate SNR (Sec. III.C) */
-  int64_t cand_capacity;  /* first-stage candidate slots kept in the workspace */
+  int64_t cand_capacity;  /* first-stage candidate slots kept in the workspace, < 2^31 */
   int64_t sample_offset;  /* global index of block sample 0 */
   int32_t block_id;       /* copied into rb_trigger.block / rb_candidate.block */
   int32_t reserved;       /* must be 0 */
@@ -150,12 +150,18 @@ int rb_basis_filter(const rb_filter_desc* desc, const rb_basis* basis, const flo
                     void* stream);
 
 /*
- * rb_pack_coeff - lay out the first-stage operand from basis->coeff for desc->precision:
- *   rows 2t and 2t+1 hold [Re a_t, Im a_t] and [-Im a_t, Re a_t] (k values each, zero
- *   padded to kp), so that one real GEMM row pair gives Re and Im of sum_k a_tk^* beta_k;
- *   split precisions store a hi plane then a lo plane (lo = round(x - hi)).
- *   out: plan.coeff_op_bytes bytes (2 planes x 2T x kp 16-bit values). Enqueue only.
- *   Errors: RB_ERR_BAD_INPUT for RB_PREC_FP32 (no operand needed) or size mismatch.
+ * rb_pack_coeff - lay out the coefficient operands of both stages from basis->coeff (the
+ * a_tk of Eq. 7). Required before rb_filter, rb_stage1 (16-bit precisions) and rb_stage2.
+ *   Second-stage part (every precision; first s2 bytes of out): an FP16 hi plane then an FP16
+ *   lo plane (lo = fp16(x - hi)), each [T][2 k16] with row t = [Re a_t (k16) | Im a_t (k16)],
+ *   k16 = k rounded up to 16, zero padded; hi + lo carries FP32-level accuracy.
+ *   First-stage part (16-bit precisions only; after the second-stage part): rows 2t and 2t+1
+ *   hold [Re a_t, Im a_t] and [-Im a_t, Re a_t] (k values each, zero padded to kp), so that
+ *   one real GEMM row pair gives Re and Im of sum_k a_tk^* beta_k; split precisions store a
+ *   hi plane then a lo plane (lo = round(x - hi)).
+ *   out: plan.coeff_op_bytes device bytes, 256-byte aligned, owned by the caller and stored
+ *   as basis->coeff_op with basis->coeff_op_precision = desc->precision. Enqueue only.
+ *   Errors: RB_ERR_BAD_INPUT for a null pointer or a basis that does not match desc.
  */
 int rb_pack_coeff(const rb_filter_desc* desc, const rb_basis* basis, void* out, void* stream);
 

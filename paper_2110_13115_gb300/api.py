@@ -98,7 +98,8 @@ def rb_basis_filter(desc, basis: Basis, s_hat: torch.Tensor, keep_beta=True, ws=
 
 
 def rb_pack_coeff(desc, basis: Basis) -> Basis:
-    """Pack the first-stage operand for desc.precision into basis.coeff_op (in place)."""
+    """Pack the coefficient operands of both stages for desc.precision into basis.coeff_op
+    (in place); rb_filter and rb_stage2 need it for every precision."""
     sizes = rb_filter_plan(desc)
     op = torch.empty(sizes.coeff_op_bytes, dtype=torch.uint8, device=basis.coeff.device)
     b = basis.c_struct()

@@ -96,8 +96,8 @@ int make_geometry(const rb_filter_desc& d, Geometry* g) {
     set_detail("thresholds must be finite and >= 0");
     return RB_ERR_BAD_INPUT;
   }
-  if (d.cand_capacity < 0 || d.reserved != 0) {
-    set_detail("cand_capacity must be >= 0 and reserved must be 0");
+  if (d.cand_capacity < 0 || d.cand_capacity > INT32_MAX || d.reserved != 0) {
+    set_detail("cand_capacity must be in [0, 2^31) and reserved must be 0");
     return RB_ERR_BAD_INPUT;
   }
   if (d.precision < RB_PREC_FP32 || d.precision > RB_PREC_BF16) {
@@ -110,13 +110,15 @@ int make_geometry(const rb_filter_desc& d, Geometry* g) {
   g->n2 = 1 << (p - p / 2);
   g->n_bins = d.n / (2 * d.w);
   g->kp = ((2 * d.k + 63) / 64) * 64;
+  g->k16 = (d.k + 15) / 16 * 16;
+  g->s2_bytes = (size_t)2 * d.n_templates * (2 * g->k16) * 2;
   return RB_OK;
 }
 
 size_t coeff_op_bytes(const rb_filter_desc& d, const Geometry& g) {
-  if (d.precision == RB_PREC_FP32) return 0;
   const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
-  return (split ? 2 : 1) * (size_t)2 * d.n_templates * g.kp * 2;
+  const size_t stage1 = d.precision == RB_PREC_FP32 ? 0 : (split ? 2 : 1) * (size_t)2 * d.n_templates * g.kp * 2;
+  return g.s2_bytes + stage1;
 }
 
 void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws, bool plain) {
@@ -158,6 +160,9 @@ void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws
     ws->cand_sorted = (rb_candidate*)take(sizeof(rb_candidate) * (size_t)std::max<int64_t>(d.cand_capacity, 1));
     ws->bin_count = (unsigned*)take(sizeof(unsigned) * (size_t)(g.n_bins + 1));
     ws->bin_start = (unsigned*)take(sizeof(unsigned) * (size_t)(g.n_bins + 1));
+    // pieces: sum over bins of ceil(c_b / kStage2Piece) <= n_bins + capacity / kStage2Piece
+    ws->pieces = (int4*)take(sizeof(int4) * (size_t)(g.n_bins + d.cand_capacity / kStage2Piece + 1));
+    ws->piece_total = (unsigned*)take(sizeof(unsigned));
   }
   ws->total = off;
 }
@@ -193,9 +198,13 @@ int read_status(const Workspace& ws, Status* s, cudaStream_t st) {
   return RB_OK;
 }
 
-int check_basis(const rb_filter_desc& d, const rb_basis* b) {
+int check_basis(const rb_filter_desc& d, const rb_basis* b, bool need_op = false) {
   if (!b || !b->vectors || !b->coeff) {
     set_detail("basis or its arrays are NULL");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (need_op && !b->coeff_op) {
+    set_detail("basis->coeff_op is NULL: pack it with rb_pack_coeff first");
     return RB_ERR_BAD_INPUT;
   }
   if (b->k < d.k || b->n_templates != d.n_templates || b->n != d.n) {
@@ -326,8 +335,8 @@ int rb_pack_coeff(const rb_filter_desc* desc, const rb_basis* basis, void* out, 
   int rc = make_geometry(*desc, &g);
   if (rc) return rc;
   if ((rc = check_basis(*desc, basis))) return rc;
-  if (desc->precision == RB_PREC_FP32 || !out) {
-    set_detail("no packed operand for FP32 (or out is NULL)");
+  if (!out || (reinterpret_cast<uintptr_t>(out) & 255)) {
+    set_detail("out is NULL or not 256-byte aligned");
     return RB_ERR_BAD_INPUT;
   }
   return pack_coeff(*desc, *basis, g, out, (cudaStream_t)stream);
@@ -415,7 +424,7 @@ int rb_stage2(const rb_filter_desc* desc, const rb_basis* basis, const float* be
   Workspace ws;
   int rc = prepare(desc, workspace, workspace_bytes, false, &g, &ws, st);
   if (rc) return rc;
-  if ((rc = check_basis(*desc, basis))) return rc;
+  if ((rc = check_basis(*desc, basis, true))) return rc;
   if (!beta || (n_cand > 0 && !cand) || !n_trig || capacity < 0 || n_cand < 0 || (capacity > 0 && !trig)) {
     set_detail("NULL array or negative count");
     return RB_ERR_BAD_INPUT;
@@ -445,7 +454,7 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
   Workspace ws;
   int rc = prepare(desc, workspace, workspace_bytes, false, &g, &ws, st);
   if (rc) return rc;
-  if ((rc = check_basis(*desc, basis))) return rc;
+  if ((rc = check_basis(*desc, basis, true))) return rc;
   if (!strain || !psd || !n_trig || capacity < 0 || (capacity > 0 && !trig)) {
     set_detail("NULL array or negative capacity");
     return RB_ERR_BAD_INPUT;

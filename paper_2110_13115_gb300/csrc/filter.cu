@@ -326,6 +326,33 @@ __global__ void k_pack_coeff(const float2* __restrict__ coeff, int ldk, int T, i
   }
 }
 
+// second-stage operand rows t: [Re a_t(0..k), 0.., Im a_t(0..k), 0..] with halves of k16 columns
+__global__ void k_pack_s2(const float2* __restrict__ coeff, int ldk, int T, int k, int k16, __half* __restrict__ hi,
+                          __half* __restrict__ lo) {
+  const int64_t p2 = 2 * (int64_t)k16;
+  const int64_t total = (int64_t)T * p2;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = idx / p2;
+    // row position p = 32 q + 8 t4 + s holds column c = 16 kc + j of [Re a (k16) | Im a (k16)] with
+    // kc = 2 q + s / 4 and j = 2 t4 + (s & 1) + 8 ((s >> 1) & 1): the m16n8k16 A-fragment order, so
+    // that one 16-byte load gives a lane its registers a0, a2 (or a1, a3) for two K chunks
+    const int pos = (int)(idx - t * p2);
+    const int q = pos >> 5, t4 = (pos >> 3) & 3, sl = pos & 7;
+    const int col = (2 * q + (sl >> 2)) * 16 + 2 * t4 + (sl & 1) + 8 * ((sl >> 1) & 1);
+    const bool im = col >= k16;
+    const int kk = im ? col - k16 : col;
+    float x = 0.f;
+    if (kk < k) {
+      const float2 a = coeff[t * ldk + kk];
+      x = im ? a.y : a.x;
+    }
+    const __half h = __float2half_rn(x);
+    hi[idx] = h;
+    lo[idx] = __float2half_rn(x - __half2float(h));
+  }
+}
+
 // beta_avg [k][nb] complex -> [nb][kp] rows: [Re beta_avg(:, i), Im beta_avg(:, i), 0..]
 template <typename T16>
 __global__ void __launch_bounds__(256) k_pack_beta(const float2* __restrict__ bavg, int k, int nb, int kp,
@@ -539,7 +566,17 @@ int pack_beta(const rb_filter_desc& d, const Geometry& g, const float2* bavg, vo
   return RB_OK;
 }
 
-int pack_coeff(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, void* out, cudaStream_t st) {
+int pack_coeff(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, void* out_all, cudaStream_t st) {
+  {
+    // second-stage operand: rows [Re a_t (k16), Im a_t (k16)] as FP16 hi and lo planes
+    const int64_t p2 = (int64_t)d.n_templates * 2 * g.k16;
+    auto* h2 = (__half*)out_all;
+    k_pack_s2<<<(int)std::min<int64_t>(4096, (p2 + 255) / 256), 256, 0, st>>>(
+        reinterpret_cast<const float2*>(b.coeff), b.k, d.n_templates, d.k, g.k16, h2, h2 + p2);
+    RB_LAUNCH_CHECK();
+  }
+  if (d.precision == RB_PREC_FP32) return RB_OK;
+  void* out = (char*)out_all + g.s2_bytes;
   const int64_t plane = (int64_t)2 * d.n_templates * g.kp;
   const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
   const bool bf = d.precision == RB_PREC_BF16 || d.precision == RB_PREC_BF16_SPLIT;

@@ -453,7 +453,7 @@ int build_params(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry&
   const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
   const bool bf = d.precision == RB_PREC_BF16 || d.precision == RB_PREC_BF16_SPLIT;
   const int64_t M = 2 * (int64_t)d.n_templates;
-  const uint16_t* a0 = (const uint16_t*)b.coeff_op;
+  const uint16_t* a0 = (const uint16_t*)((const char*)b.coeff_op + g.s2_bytes);
   const uint16_t* a1 = split ? a0 + M * g.kp : a0;
   int rc;
   if ((rc = make_map(&maps[0], a0, bf, g.kp, M, BM))) return rc;

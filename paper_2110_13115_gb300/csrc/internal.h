@@ -9,11 +9,16 @@
 
 namespace rb {
 
+// Second-stage work item: at most this many bucketed candidates of one bin.
+constexpr unsigned kStage2Piece = 512;
+
 struct Geometry {
   int64_t n = 0;       // block length
   int n1 = 0, n2 = 0;  // four-step split n = n1 * n2 (outer x inner)
   int64_t n_bins = 0;  // valid bins n / (2 w)
   int kp = 0;          // 2k rounded up to 64 (first-stage contraction length)
+  int k16 = 0;         // k rounded up to 16 (second-stage chunking)
+  size_t s2_bytes = 0; // second-stage operand planes at the start of coeff_op
 };
 
 struct Tables {
@@ -44,6 +49,8 @@ struct Workspace {
   rb_candidate* cand_sorted = nullptr;  // candidates grouped by bin for the second stage
   unsigned* bin_count = nullptr;        // [n_bins + 1] per-bin counts, then fill cursors
   unsigned* bin_start = nullptr;        // [n_bins + 1] exclusive prefix sums
+  int4* pieces = nullptr;               // second-stage work items {bin, first, end, 0}
+  unsigned* piece_total = nullptr;      // number of pieces (device)
   size_t total = 0;
 };
 

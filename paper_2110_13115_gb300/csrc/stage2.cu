@@ -3,14 +3,18 @@
 //
 // 1. First-stage candidates are bucketed by bin: per-bin counts (warp-aggregated atomics), an
 //    exclusive scan, and a scatter.
-// 2. One CTA per bin stages the bin's k x w window of beta once, as 16-bit hi + lo tensor-core
-//    fragments of the real contraction
+// 2. The scan cuts each non-empty bin into pieces of at most kStage2Piece candidates, so a bin
+//    with thousands of candidates is shared by many CTAs and empty bins cost nothing. For each
+//    piece a CTA stages the bin's k x w window of beta (unless it already holds that bin) as
+//    16-bit hi + lo tensor-core fragments of the real contraction
 //        B[kk][2r]   = kk < k ? Re beta_kk[m0 + r] :  Im beta_(kk-k)[m0 + r]
 //        B[kk][2r+1] = kk < k ? Im beta_kk[m0 + r] : -Re beta_(kk-k)[m0 + r],
 //    so that [Re a_t, Im a_t] . B gives (Re, Im) of z_t[m0 + r] = sum_k conj(a_tk) beta_k[m0 + r].
 //    Each warp reconstructs 16 candidates at a time with mma.sync m16n8k16 (FP16 in, FP32
 //    accumulate) using three products hi.hi + hi.lo + lo.hi, which keeps the result at FP32
-//    accuracy; coefficients are read in FP32 and split on the fly.
+//    accuracy; the coefficients come pre-split from rb_pack_coeff (rows [Re a, Im a] in FP16
+//    hi and lo planes at the start of coeff_op, columns permuted into fragment order so that
+//    each lane fetches its A registers for two K chunks with one 16-byte load).
 // 3. The arg-max over the bin's w samples (first on ties) is kept when |z| >= rho_II.
 #include <cuda_fp16.h>
 
@@ -22,6 +26,7 @@
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kPiece = rb::kStage2Piece;  // candidates per second-stage work item
 
 // Per-bin counts; lanes holding the same bin combine into one atomic.
 __global__ void k_bin_count(const rb_candidate* __restrict__ cand, const unsigned long long* dev_count, int64_t cap,
@@ -38,51 +43,60 @@ __global__ void k_bin_count(const rb_candidate* __restrict__ cand, const unsigne
   }
 }
 
-// Exclusive scan of count[0, nb) into start[0, nb]; count is reset to zero (it becomes the
-// per-bin fill cursor). One CTA of 1024 threads walks the array in tiles of 8192 counters,
-// each thread scanning 8 consecutive ones, with a running carry between tiles.
-__global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count, unsigned* __restrict__ start, int nb) {
-  __shared__ unsigned wsum[32];
-  __shared__ unsigned carry_s;
+// Exclusive scan of count[0, nb) into start[0, nb] plus the piece list; count is reset to zero
+// (it becomes the per-bin fill cursor). A bin holding c candidates is cut into ceil(c / kPiece)
+// pieces {bin, first, end} of at most kPiece consecutive bucketed candidates, so that the
+// second stage can spread a bin with thousands of candidates over many CTAs and skips empty
+// bins entirely. Counts and piece counts are scanned together as one 64-bit value (pieces in the
+// high word). One CTA of 1024 threads walks the array in tiles of 8192 counters, each thread
+// scanning 8 consecutive ones, with a running carry between tiles.
+__global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count, unsigned* __restrict__ start, int nb,
+                                                   int4* __restrict__ pieces, unsigned* __restrict__ piece_total) {
+  using u64 = unsigned long long;
+  __shared__ u64 wsum[32];
+  __shared__ u64 carry_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) carry_s = 0;
   __syncthreads();
   for (int base = 0; base < nb; base += 8192) {
-    unsigned v[8];
-    unsigned s = 0;
+    u64 v[8];
+    u64 s = 0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int i = base + tid * 8 + j;
-      v[j] = i < nb ? count[i] : 0u;
+      const unsigned c = i < nb ? count[i] : 0u;
+      v[j] = (u64)c | ((u64)((c + kPiece - 1) / kPiece) << 32);
       s += v[j];
     }
-    unsigned inc = s;
+    u64 inc = s;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const unsigned y = __shfl_up_sync(kFull, inc, off);
+      const u64 y = __shfl_up_sync(kFull, inc, off);
       if (lane >= off) inc += y;
     }
     if (lane == 31) wsum[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-      const unsigned x0 = wsum[lane];
-      unsigned x = x0;
+      const u64 x0 = wsum[lane];
+      u64 x = x0;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
-        const unsigned y = __shfl_up_sync(kFull, x, off);
+        const u64 y = __shfl_up_sync(kFull, x, off);
         if (lane >= off) x += y;
       }
       wsum[lane] = x - x0;
     }
     __syncthreads();
-    const unsigned carry = carry_s;
-    unsigned run = carry + wsum[warp] + inc - s;
+    u64 run = carry_s + wsum[warp] + inc - s;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int i = base + tid * 8 + j;
       if (i < nb) {
-        start[i] = run;
+        const unsigned c0 = (unsigned)run, c = (unsigned)v[j], p0 = (unsigned)(run >> 32);
+        start[i] = c0;
         count[i] = 0;
+        for (unsigned q = 0; q * kPiece < c; ++q)
+          pieces[p0 + q] = make_int4(i, (int)(c0 + q * kPiece), (int)(c0 + min(c, (q + 1) * kPiece)), 0);
       }
       run += v[j];
     }
@@ -90,7 +104,10 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
     if (tid == 1023) carry_s = run;
     __syncthreads();
   }
-  if (tid == 0) start[nb] = carry_s;
+  if (tid == 0) {
+    start[nb] = (unsigned)carry_s;
+    *piece_total = (unsigned)(carry_s >> 32);
+  }
 }
 
 __global__ void k_bin_scatter(const rb_candidate* __restrict__ cand, const unsigned long long* dev_count, int64_t cap,
@@ -141,53 +158,69 @@ struct S2 {
   static constexpr int NT = (2 * W + 7) / 8;
 };
 
-// Shared memory per bin: window [W][k16] float2, then fragments frag[plane][kc][nt][lane] (uint2).
+// Stages the k x W window of beta starting at valid-half index m0 into shared memory, then
+// writes its hi and lo tensor-core B fragments; ends with a barrier. The B operand of
+// m16n8k16 for lane L holds b0 = (kk = 16 kc + 2 t, +1), b1 = (+8, +9) of column n = 8 nt + g.
 template <int W>
-__global__ void __launch_bounds__(256) k_stage2_bins(const float2* __restrict__ coeff, int ldk,
+__device__ __forceinline__ void stage_window(const float2* __restrict__ beta, int64_t m0, int64_t half, int k,
+                                             int k16, float2* win, uint2* frag) {
+  constexpr int NT = S2<W>::NT;
+  const int pitch = k16 + 1, nkc = 2 * k16 / 16;
+  for (int idx = threadIdx.x; idx < k16 * W; idx += blockDim.x) {
+    const int kk = idx / W, r = idx - kk * W;
+    win[r * pitch + kk] = kk < k ? __ldg(beta + (int64_t)kk * half + m0 + r) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nkc * NT * 32; idx += blockDim.x) {
+    const int L = idx & 31, nt = (idx >> 5) % NT, kc = (idx >> 5) / NT;
+    const int gg = L >> 2, tt = L & 3;
+    const int n = nt * 8 + gg, r = n >> 1, part = n & 1;
+    __half hv[4], lv[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int kk = kc * 16 + 2 * tt + (e & 1) + (e >> 1) * 8;
+      float x = 0.f;
+      if (r < W) {
+        const bool im_half = kk >= k16;
+        const float2 bv = win[r * pitch + (im_half ? kk - k16 : kk)];
+        x = !im_half ? (part ? bv.y : bv.x) : (part ? -bv.x : bv.y);
+      }
+      split_h(x, hv[e], lv[e]);
+    }
+    frag[((0 * nkc + kc) * NT + nt) * 32 + L] = make_uint2(pack_h2(hv[0], hv[1]), pack_h2(hv[2], hv[3]));
+    frag[((1 * nkc + kc) * NT + nt) * 32 + L] = make_uint2(pack_h2(lv[0], lv[1]), pack_h2(lv[2], lv[3]));
+  }
+  __syncthreads();
+}
+
+// Shared memory per bin: window [W][k16 + 1] float2, then fragments frag[plane][kc][nt][lane] (uint2).
+template <int W>
+__global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict__ ahi, const __half* __restrict__ alo,
                                                      const float2* __restrict__ beta, int k, int k16, int T,
-                                                     int64_t half, int bin0, int nb,
-                                                     const unsigned* __restrict__ start,
+                                                     int64_t half, int bin0, const int4* __restrict__ pieces,
+                                                     const unsigned* __restrict__ piece_total,
                                                      const rb_candidate* __restrict__ sorted, float thr2,
                                                      int64_t sample_offset, rb_trigger* __restrict__ trig,
                                                      unsigned long long* counter, int64_t cap) {
   constexpr int NT = S2<W>::NT;
   extern __shared__ __align__(16) uint8_t s2mem[];
-  float2* win = reinterpret_cast<float2*>(s2mem);  // [W][k16]
-  const int nkc = 2 * k16 / 16;                     // K chunks: Re half then Im half
-  uint2* frag = reinterpret_cast<uint2*>(s2mem + sizeof(float2) * W * k16);  // [2][nkc][NT][32]
+  const int pitch = k16 + 1;                        // padded window rows (bank spread)
+  float2* win = reinterpret_cast<float2*>(s2mem);  // [W][pitch]
+  const int nkc = 2 * k16 / 16;                     // K chunks: Re half then Im half (even)
+  uint2* frag = reinterpret_cast<uint2*>(s2mem + sizeof(float2) * W * pitch);  // [2][nkc][NT][32]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int g = lane >> 2, t4 = lane & 3;
-  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-    const unsigned c0 = start[b], c1 = start[b + 1];
-    if (c0 == c1) continue;
-    __syncthreads();
-    const int64_t m0 = (int64_t)(bin0 + b) * W - half;
-    for (int idx = threadIdx.x; idx < k16 * W; idx += blockDim.x) {
-      const int kk = idx / W, r = idx - kk * W;
-      win[r * k16 + kk] = kk < k ? __ldg(beta + (int64_t)kk * half + m0 + r) : make_float2(0.f, 0.f);
+  const unsigned npieces = *piece_total;
+  int staged = -1;
+  for (unsigned p = blockIdx.x; p < npieces; p += gridDim.x) {
+    const int4 pc = pieces[p];
+    const int b = pc.x;
+    const unsigned c0 = (unsigned)pc.y, c1 = (unsigned)pc.z;
+    if (b != staged) {  // block-uniform: the window and its fragments change with the bin
+      staged = b;
+      __syncthreads();  // every warp is done with the previous bin's fragments
+      stage_window<W>(beta, (int64_t)(bin0 + b) * W - half, half, k, k16, win, frag);
     }
-    __syncthreads();
-    // B fragments: element (kk, n) for lane L: b0 = (kk = 16kc + 2t, +1), b1 = (+8, +9); n = 8 nt + g
-    for (int idx = threadIdx.x; idx < nkc * NT * 32; idx += blockDim.x) {
-      const int L = idx & 31, nt = (idx >> 5) % NT, kc = (idx >> 5) / NT;
-      const int gg = L >> 2, tt = L & 3;
-      const int n = nt * 8 + gg, r = n >> 1, part = n & 1;
-      __half hv[4], lv[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int kk = kc * 16 + 2 * tt + (e & 1) + (e >> 1) * 8;
-        float x = 0.f;
-        if (r < W) {
-          const bool im_half = kk >= k16;
-          const float2 bv = win[r * k16 + (im_half ? kk - k16 : kk)];
-          x = !im_half ? (part ? bv.y : bv.x) : (part ? -bv.x : bv.y);
-        }
-        split_h(x, hv[e], lv[e]);
-      }
-      frag[((0 * nkc + kc) * NT + nt) * 32 + L] = make_uint2(pack_h2(hv[0], hv[1]), pack_h2(hv[2], hv[3]));
-      frag[((1 * nkc + kc) * NT + nt) * 32 + L] = make_uint2(pack_h2(lv[0], lv[1]), pack_h2(lv[2], lv[3]));
-    }
-    __syncthreads();
     for (unsigned base = c0 + warp * 16; base < c1; base += nwarp * 16) {
       // rows g and g + 8 of the m16 tile are candidates base + g and base + g + 8
       int tr[2];
@@ -200,28 +233,26 @@ __global__ void __launch_bounds__(256) k_stage2_bins(const float2* __restrict__ 
       float d[NT][4];
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.f;
-      for (int c = 0; c < k16 / 16; ++c) {
-        // coefficients a[16c + 2t + {0, 1, 8, 9}] of the two rows, FP32 -> hi/lo halves
-        float2 av[2][4];
+      // A fragments straight from the packed FP16 hi/lo rows, stored in fragment order: the 16 bytes
+      // at 32 q + 8 t4 of a row hold this lane's (a0, a2) for K chunks 2q and 2q + 1
+      const int64_t p2 = 2 * (int64_t)k16;
+      const uint4* rh0 = reinterpret_cast<const uint4*>(ahi + (int64_t)max(tr[0], 0) * p2) + t4;
+      const uint4* rh1 = reinterpret_cast<const uint4*>(ahi + (int64_t)max(tr[1], 0) * p2) + t4;
+      const uint4* rl0 = reinterpret_cast<const uint4*>(alo + (int64_t)max(tr[0], 0) * p2) + t4;
+      const uint4* rl1 = reinterpret_cast<const uint4*>(alo + (int64_t)max(tr[1], 0) * p2) + t4;
+      const bool v0 = tr[0] >= 0, v1 = tr[1] >= 0;
+      const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll 2
+      for (int q = 0; q < nkc / 2; ++q) {
+        const uint4 h0 = v0 ? __ldg(rh0 + 4 * q) : z4, h1 = v1 ? __ldg(rh1 + 4 * q) : z4;
+        const uint4 l0 = v0 ? __ldg(rl0 + 4 * q) : z4, l1 = v1 ? __ldg(rl1 + 4 * q) : z4;
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int kk = c * 16 + 2 * t4 + (e & 1) + (e >> 1) * 8;
-            av[h][e] = (tr[h] >= 0 && kk < k) ? __ldg(coeff + (int64_t)tr[h] * ldk + kk) : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-        for (int part = 0; part < 2; ++part) {  // Re half (chunk c), then Im half (chunk k16/16 + c)
-          __half hh[2][4], ll[2][4];
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) split_h(part ? av[h][e].y : av[h][e].x, hh[h][e], ll[h][e]);
-          const uint32_t ah0 = pack_h2(hh[0][0], hh[0][1]), ah1 = pack_h2(hh[1][0], hh[1][1]);
-          const uint32_t ah2 = pack_h2(hh[0][2], hh[0][3]), ah3 = pack_h2(hh[1][2], hh[1][3]);
-          const uint32_t al0 = pack_h2(ll[0][0], ll[0][1]), al1 = pack_h2(ll[1][0], ll[1][1]);
-          const uint32_t al2 = pack_h2(ll[0][2], ll[0][3]), al3 = pack_h2(ll[1][2], ll[1][3]);
-          const int kc = part * (k16 / 16) + c;
+        for (int half_q = 0; half_q < 2; ++half_q) {
+          const int kc = 2 * q + half_q;
+          const uint32_t ah0 = half_q ? h0.z : h0.x, ah2 = half_q ? h0.w : h0.y;
+          const uint32_t ah1 = half_q ? h1.z : h1.x, ah3 = half_q ? h1.w : h1.y;
+          const uint32_t al0 = half_q ? l0.z : l0.x, al2 = half_q ? l0.w : l0.y;
+          const uint32_t al1 = half_q ? l1.z : l1.x, al3 = half_q ? l1.w : l1.y;
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt) {
             const uint2 bh = frag[((0 * nkc + kc) * NT + nt) * 32 + lane];
@@ -295,17 +326,18 @@ int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& 
   const int nb = (int)g.n_bins;
   const int k16 = (d.k + 15) / 16 * 16;
   const int nkc = 2 * k16 / 16;
-  const int smem = (int)(sizeof(float2) * W * k16 + sizeof(uint2) * 2 * nkc * NT * 32);
+  const int smem = (int)(sizeof(float2) * W * (k16 + 1) + sizeof(uint2) * 2 * nkc * NT * 32);
   if (smem > 200 * 1024) {
     rb::set_detail("k * w too large for the second-stage window (%d x %d)", d.k, W);
     return RB_ERR_UNSUPPORTED;
   }
   auto kern = k_stage2_bins<W>;
   if (smem > 48 * 1024) RB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  const int grid = std::min(nb, 152 * 8);
-  kern<<<grid, 256, smem, st>>>(reinterpret_cast<const float2*>(b.coeff), b.k, beta, d.k, k16, d.n_templates,
-                                g.n / 2, nb, nb, ws.bin_start, ws.cand_sorted, d.rho_ii * d.rho_ii, d.sample_offset,
-                                trig, ws.trig_count, cap);
+  const int grid = 152 * 8;
+  const __half* ahi = reinterpret_cast<const __half*>(b.coeff_op);
+  const __half* alo = ahi + (int64_t)d.n_templates * 2 * k16;
+  kern<<<grid, 256, smem, st>>>(ahi, alo, beta, d.k, k16, d.n_templates, g.n / 2, nb, ws.pieces, ws.piece_total,
+                                ws.cand_sorted, d.rho_ii * d.rho_ii, d.sample_offset, trig, ws.trig_count, cap);
   RB_LAUNCH_CHECK();
   return RB_OK;
 }
@@ -321,7 +353,7 @@ int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& 
   RB_CUDA_TRY(cudaMemsetAsync(ws.bin_count, 0, sizeof(unsigned) * (nb + 1), st));
   k_bin_count<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, nb, ws.bin_count);
   RB_LAUNCH_CHECK();
-  k_bin_scan<<<1, 1024, 0, st>>>(ws.bin_count, ws.bin_start, nb);
+  k_bin_scan<<<1, 1024, 0, st>>>(ws.bin_count, ws.bin_start, nb, ws.pieces, ws.piece_total);
   RB_LAUNCH_CHECK();
   k_bin_scatter<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, nb, ws.bin_start,
                                          ws.bin_count, ws.cand_sorted);

@@ -93,7 +93,10 @@ def test_plan_validation(lib):
     assert plan(precision=9)[0] == N.RB_ERR_UNSUPPORTED
     rc, s2 = plan(n=524288, k=256, n_templates=10000, precision="fp16_split")
     assert rc == 0 and (s2.n1, s2.n2, s2.kp) == (512, 1024, 512)
-    assert s2.coeff_op_bytes == 2 * 2 * 10000 * 512 * 2
+    # second-stage planes (hi, lo) of [T][2 k16] FP16, then first-stage planes (2 x 2T x kp)
+    assert s2.coeff_op_bytes == 2 * 10000 * 512 * 2 + 2 * 2 * 10000 * 512 * 2
+    rc, s3 = plan(n=524288, k=256, n_templates=10000, precision="fp32")
+    assert rc == 0 and s3.coeff_op_bytes == 2 * 10000 * 512 * 2
     # beta (k n/2 complex64) dominates the workspace
     assert s2.workspace_bytes >= 256 * 262144 * 8
     assert lib.rb_strerror(N.RB_ERR_OVERFLOW) == b"output overflow"

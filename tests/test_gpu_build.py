@@ -99,6 +99,7 @@ def test_pipeline_real_bank_vs_oracle_rb(api, k, w, rho_i):
     basis = api.rb_build(b, psd_d, k, oversample=64, power_iters=1)
     rho_ii = 5.0
     d = api.make_desc(g.fs, g.n, k, len(wl.bank), w=w, rho_i=rho_i, rho_ii=rho_ii, cand_capacity=1 << 18)
+    api.rb_pack_coeff(d, basis)
     buf, nt = api.rb_filter(d, basis, torch.from_numpy(wl.strain).cuda(), psd_d)
     got = api.triggers_numpy(buf, nt)
     hs = W.bank_templates(wl.bank, g.fs, g.n, g.f_low, 2)

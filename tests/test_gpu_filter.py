@@ -140,6 +140,7 @@ def test_stage2_parity(api, w):
     cands = np.unique(cands)
     d = api.make_desc(1024.0, n, k, T, w=w, rho_ii=2.2)
     basis = api.Basis(_dev(np.zeros((k, half), np.complex64)), _dev(a), n)
+    api.rb_pack_coeff(d, basis)
     cbuf = _dev(cands.view(np.uint8))
     buf, nt = api.rb_stage2(d, basis, _dev(beta), cbuf, len(cands))
     got = api.triggers_numpy(buf, nt)
@@ -165,6 +166,7 @@ def test_filter_end_to_end_fp32(api, n, k, T, w):
     rho_i, rho_ii = 2.2 / np.sqrt(w), 3.0
     d = api.make_desc(g.fs, n, k, T, w=w, rho_i=rho_i, rho_ii=rho_ii, cand_capacity=1 << 18)
     basis = api.Basis(_dev(P), _dev(a), n)
+    api.rb_pack_coeff(d, basis)
     buf, nt = api.rb_filter(d, basis, _dev(x), _dev(psd))
     got = api.triggers_numpy(buf, nt)
     s_fd = mf.strain_fd(x.astype(np.float64), g.fs)

@@ -50,8 +50,7 @@ def test_static_scratch_matches_workspace_path(api, prec):
     basis = api.rb_build(api.Bank(wl.bank, g.fs, g.n, g.f_low, 2), psd, k, oversample=64, power_iters=1)
     d = api.make_desc(g.fs, g.n, k, len(wl.bank), w=w, precision=prec, rho_i=2.5, rho_ii=4.0,
                       cand_capacity=1 << 16)
-    if prec != "fp32":
-        api.rb_pack_coeff(d, basis)
+    api.rb_pack_coeff(d, basis)
     assert api.rb_filter_plan(d).workspace_bytes <= (32 << 20)
     cap = 1 << 16
     ref_buf, n_ref = api.rb_filter(d, basis, strain, psd, capacity=cap)
