@@ -313,13 +313,16 @@ def main():
     ws = api.workspace(d)
     tuned = None
     api.rb_pack_coeff(d, basis)
+    # autotune the FFT schedule and the first stage's tile variant on this block (setup, untimed)
+    sh = api.rb_whiten(d, strain_d, psd_d, ws=ws)
+    fft_choice, fft_times = api.rb_tune_fft(d, basis, sh, ws=ws)
+    fft_tuned = dict(variant=fft_choice, ms_by_variant=[round(t, 4) for t in fft_times])
     if args.precision != "fp32":
-        # autotune the first stage's tile variant on this block's operands (setup, untimed)
-        sh = api.rb_whiten(d, strain_d, psd_d, ws=ws)
         _, bavg_t = api.rb_basis_filter(d, basis, sh, keep_beta=False, ws=ws)
         chosen, times = api.rb_tune_stage1(d, basis, bavg_t, ws=ws)
         tuned = dict(variant=chosen, n_tile=[256, 128][chosen], ms_by_variant=times)
-        del sh, bavg_t
+        del bavg_t
+    del sh
     cap = 1 << 23
     trig = torch.empty(cap * 24, dtype=torch.uint8, device="cuda")
 
@@ -450,7 +453,7 @@ def main():
                            k=args.k, w=args.w, rho_I=rho_i, rho_II=wl.rho_ii, first_stage=args.precision,
                            rho_I_calibration=f"noise-only block, {n_cal} flat triggers, recovery {args.recovery}",
                            l2="inputs larger than L2: the basis alone is 537 MB per step",
-                           first_stage_tile=tuned,
+                           first_stage_tile=tuned, fft_schedule=fft_tuned,
                            parallelism=f"replicas x{world} (one block per GPU)"),
                roofline=roof, cpu_baseline=cpu,
                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h_total // args.steps),

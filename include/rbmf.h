@@ -15,9 +15,9 @@
  *    In them the inner product <a|b> of Eq. (1) is sum_j a_hat[j] conj(b_hat[j]).
  *  - Complex arrays are interleaved float pairs (re, im), C order as stated per argument.
  *  - Pointers are DEVICE pointers unless the argument says "host". All buffers are owned
- *    by the caller; the library allocates no device memory: every call that needs scratch
- *    space takes a caller-provided workspace of at least the size rb_filter_plan reports
- *    (256-byte aligned).
+ *    by the caller; the library allocates no device memory (beyond the CUDA graph objects that
+ *    rb_batch_create records): every call that needs scratch space takes a caller-provided
+ *    workspace of at least the size rb_filter_plan reports (256-byte aligned).
  *  - `stream` is a cudaStream_t (NULL = legacy default stream). Calls that return counts
  *    (n_out) synchronise that stream before returning; the others only enqueue work.
  *  - Every function returns RB_OK (0) or a negative RB_ERR_* code; nothing throws.
@@ -76,7 +76,7 @@ typedef struct rb_basis {
   int64_t n;              /* block length the basis was built for */
   const float* vectors;   /* [k][n/2] complex: p_k in whitened coordinates, orthonormal */
   const float* coeff;     /* [T][k] complex: a_tk = <g_t|p_k> / sigma_t (SNR units, Eq. 7) */
-  const void* coeff_op;   /* packed first-stage operand from rb_pack_coeff (NULL for FP32) */
+  const void* coeff_op;   /* packed stage operands from rb_pack_coeff (needed by rb_filter, rb_stage2) */
   int32_t coeff_op_precision; /* RB_PREC_* coeff_op was packed for */
   int32_t reserved;
 } rb_basis;
@@ -104,7 +104,7 @@ typedef struct rb_filter_sizes {
   int64_t n_bins;           /* valid bins n/(2w) */
   int32_t n1, n2;           /* four-step split n = n1 * n2 */
   int32_t kp;               /* stage-1 contraction length 2k rounded up to 64 */
-  size_t coeff_op_bytes;    /* bytes rb_pack_coeff writes for desc->precision (0 for FP32) */
+  size_t coeff_op_bytes;    /* bytes rb_pack_coeff writes for desc->precision */
 } rb_filter_sizes;
 
 /* Name of a status code (static string). */
@@ -242,6 +242,68 @@ int rb_filter_static(const rb_filter_desc* desc, const rb_basis* basis, const fl
                      rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* stream);
 
 /*
+ * Batching: many blocks - from segments of uneven length, several detectors and several FFT sizes -
+ * filtered in one call, each block through the whole rb_filter pipeline (Sec. III.E: the data of
+ * many segments is processed per launch so that the device never idles between them). Banks that
+ * share a basis are filtered together by concatenating their coefficient rows (the M dimension of
+ * the first-stage GEMM), so each block's basis series beta is computed once for all of them.
+ *
+ * rb_block - one filtering block:
+ *   strain: device [n] float32 samples of the block; psd: device [n/2 + 1] float64 one-sided PSD of
+ *   its detector (a per-detector scale factor is a scaled PSD).
+ *   basis: index into the descs / bases arrays (one entry per FFT size n; entry i's desc describes
+ *   bases[i]); its desc's sample_offset and block_id are replaced by the block's own.
+ *   valid_lo: first block sample whose triggers are kept, n/2 <= valid_lo < n, a multiple of w:
+ *   n/2 for an ordinary block, more for a right-aligned tail block whose leading valid samples the
+ *   previous block already covered (no trigger is reported twice).
+ */
+typedef struct rb_block {
+  const float* strain;
+  const double* psd;
+  int64_t sample_offset;
+  int64_t valid_lo;
+  int32_t basis;
+  int32_t block_id;
+} rb_block;
+
+/* rb_batch_plan - workspace bytes for batches over descs[0..n_descs): the largest rb_filter_plan
+ * workspace (blocks run one after another through one workspace). Errors as rb_filter_plan. */
+int rb_batch_plan(const rb_filter_desc* descs, int32_t n_descs, size_t* workspace_bytes);
+
+/*
+ * rb_filter_batch - filter blocks[0..n_blocks) in order, appending every block's triggers to trig
+ * (one counter; trigger order across blocks is unspecified) and synchronising once at the end.
+ *   descs, bases: n_bases pairs, each bases[i] packed (rb_pack_coeff) for descs[i].
+ *   trig: [capacity] device output; n_trig (host): triggers found.
+ *   Errors: RB_ERR_BAD_INPUT (a block's basis index, pointers, valid_lo; a basis that does not match
+ *   its desc; a PSD that is not finite and positive), RB_ERR_OOM (workspace), RB_ERR_OVERFLOW (some
+ *   block had more than its desc's cand_capacity candidates, or more than capacity triggers in all;
+ *   *n_trig is the count found), RB_ERR_TIMEOUT, RB_ERR_CUDA.
+ */
+int rb_filter_batch(const rb_filter_desc* descs, const rb_basis* bases, int32_t n_bases, const rb_block* blocks,
+                    int64_t n_blocks, rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/*
+ * rb_batch_create / rb_batch_run / rb_batch_destroy - the same batch recorded once as a CUDA graph
+ * and replayed with a single graph launch per run. create validates the arguments as
+ * rb_filter_batch does, copies descs, bases and blocks, and records every kernel, memset and
+ * copy of the batch on a private stream; the device buffers (strain, psd, coefficients, basis,
+ * trig, workspace) are referenced, not copied: keep them alive and at the same addresses until
+ * destroy, and refill them between runs to filter new data. Record the batch after the first-stage
+ * tile choice (rb_tune_stage1 / rb_set_stage1_variant) it should use.
+ *   run: launches the graph on `stream`, then reads the status (synchronises `stream`); results and
+ *   errors as rb_filter_batch. Runs on one batch must not overlap.
+ *   out (create): a new handle, owned by the caller; destroy frees it (NULL is a no-op).
+ */
+typedef struct rb_batch rb_batch;
+int rb_batch_create(const rb_filter_desc* descs, const rb_basis* bases, int32_t n_bases, const rb_block* blocks,
+                    int64_t n_blocks, rb_trigger* trig, int64_t capacity, void* workspace, size_t workspace_bytes,
+                    rb_batch** out);
+int rb_batch_run(rb_batch* batch, int64_t* n_trig, void* stream);
+int rb_batch_destroy(rb_batch* batch);
+
+/*
  * rb_tune_stage1 - autotuner of the tensor-core first stage: packs beta_avg (as rb_stage1 does), times
  * each tile variant of the tcgen05 kernel (N-tile width 256 or 128 columns with the deepest operand
  * ring that fits in shared memory) with the threshold disabled, and remembers the fastest for this
@@ -256,6 +318,21 @@ int rb_filter_static(const rb_filter_desc* desc, const rb_basis* basis, const fl
 int rb_set_stage1_variant(const rb_filter_desc* desc, int32_t variant);
 int rb_tune_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* beta_avg, double* times_ms,
                    int32_t* chosen, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rb_tune_fft - autotuner of the FFT schedule of the basis filter (rb_basis_filter, and inside
+ * rb_filter / rb_filter_batch / rb_filter_plain): times every variant of RB_FFT_VARIANTS (columns
+ * per CTA of the two four-step passes, and the size of the chunk of vectors whose intermediate stays
+ * in L2) on this desc's basis and s_hat, and remembers the fastest for (n, w) in a process-wide
+ * table (variant 0 when untuned). Measurement support, not in the paper.
+ *   s_hat: [n/2] complex device (rb_whiten output). times_ms: HOST [RB_FFT_VARIANTS] mean ms of one
+ *   basis filter. chosen: HOST, the selected variant. Synchronises `stream`.
+ */
+#define RB_FFT_VARIANTS 6
+int rb_tune_fft(const rb_filter_desc* desc, const rb_basis* basis, const float* s_hat, double* times_ms,
+                int32_t* chosen, void* workspace, size_t workspace_bytes, void* stream);
+/* rb_set_fft_variant - pin the FFT schedule variant used for desc's (n, w). Host only. */
+int rb_set_fft_variant(const rb_filter_desc* desc, int32_t variant);
 
 /* Stages of rb_filter timed by the profiler (CUDA events recorded on the call's stream). */
 enum {

@@ -21,6 +21,7 @@ RB_ERR_CUDA = -5
 RB_ERR_UNSUPPORTED = -6
 
 RB_STAGES = 6
+RB_FFT_VARIANTS = 6
 STAGE_NAMES = ["setup", "whiten", "basis_filter", "pack", "first_stage", "second_stage"]
 
 RB_PREC_FP32 = 0
@@ -68,7 +69,12 @@ class rb_refine_desc(C.Structure):
                 ("steps", C.c_int32), ("alpha0", C.c_double), ("alpha_max", C.c_double)]
 
 
-EXTRA_STRUCTS = {"rb_bank_desc": rb_bank_desc, "rb_refine_desc": rb_refine_desc}
+class rb_block(C.Structure):
+    _fields_ = [("strain", C.c_void_p), ("psd", C.c_void_p), ("sample_offset", C.c_int64), ("valid_lo", C.c_int64),
+                ("basis", C.c_int32), ("block_id", C.c_int32)]
+
+
+EXTRA_STRUCTS = {"rb_bank_desc": rb_bank_desc, "rb_refine_desc": rb_refine_desc, "rb_block": rb_block}
 
 assert C.sizeof(rb_trigger) == 24 and C.sizeof(rb_candidate) == 16
 
@@ -91,7 +97,16 @@ SIGNATURES = {
     "rb_filter": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_plain": (C.c_int, [_D, _P, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_static": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P]),
+    "rb_batch_plan": (C.c_int, [_D, C.c_int32, C.POINTER(C.c_size_t)]),
+    "rb_filter_batch": (C.c_int, [_D, _B, C.c_int32, C.POINTER(rb_block), C.c_int64, _P, C.c_int64, _I64P, _P,
+                                  C.c_size_t, _P]),
+    "rb_batch_create": (C.c_int, [_D, _B, C.c_int32, C.POINTER(rb_block), C.c_int64, _P, C.c_int64, _P, C.c_size_t,
+                                  C.POINTER(C.c_void_p)]),
+    "rb_batch_run": (C.c_int, [_P, _I64P, _P]),
+    "rb_batch_destroy": (C.c_int, [_P]),
     "rb_set_stage1_variant": (C.c_int, [_D, C.c_int32]),
+    "rb_set_fft_variant": (C.c_int, [_D, C.c_int32]),
+    "rb_tune_fft": (C.c_int, [_D, _B, _P, C.POINTER(C.c_double), C.POINTER(C.c_int32), _P, C.c_size_t, _P]),
     "rb_tune_stage1": (C.c_int, [_D, _B, _P, C.POINTER(C.c_double), C.POINTER(C.c_int32), _P, C.c_size_t, _P]),
     "rb_refine_workspace_bytes": (C.c_size_t, [C.POINTER(rb_refine_desc)]),
     "rb_refine_eval": (C.c_int, [C.POINTER(rb_refine_desc), _P, _P, _P, _P, _P, C.c_int64, _P, C.c_size_t, _P]),

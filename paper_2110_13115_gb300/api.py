@@ -161,6 +161,100 @@ def rb_filter_plain(desc, templates: torch.Tensor, strain: torch.Tensor, psd: to
     return trig, n.value
 
 
+# --- batching -------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Block:
+    """One filtering block of a batch (see rb_block): device strain [n] float32 and PSD [n/2+1]
+    float64, the index of its (desc, basis) pair, its global sample offset, the first block
+    sample whose triggers are kept, and the id copied into its triggers."""
+
+    strain: torch.Tensor
+    psd: torch.Tensor
+    basis: int
+    sample_offset: int = 0
+    valid_lo: int | None = None  # default n/2
+    block_id: int = 0
+
+
+def _blocks(descs, blocks):
+    arr = (N.rb_block * max(len(blocks), 1))()
+    for i, b in enumerate(blocks):
+        if b.valid_lo is not None:
+            lo = int(b.valid_lo)
+        else:  # n/2 of the block's desc; an out-of-range index is left for the library to reject
+            lo = descs[b.basis].n // 2 if 0 <= b.basis < len(descs) else 0
+        arr[i] = N.rb_block(b.strain.data_ptr(), b.psd.data_ptr(), int(b.sample_offset), lo, int(b.basis),
+                            int(b.block_id))
+    return arr
+
+
+def _pairs(descs, bases):
+    assert len(descs) == len(bases) and len(descs) > 0
+    d = (N.rb_filter_desc * len(descs))(*descs)
+    b = (N.rb_basis * len(bases))(*[x.c_struct() for x in bases])
+    return d, b
+
+
+def rb_batch_plan(descs) -> int:
+    d = (N.rb_filter_desc * len(descs))(*descs)
+    out = C.c_size_t(0)
+    N.check("rb_batch_plan", _lib().rb_batch_plan(d, len(descs), C.byref(out)))
+    return out.value
+
+
+def batch_workspace(descs, device="cuda") -> torch.Tensor:
+    return torch.empty(rb_batch_plan(descs), dtype=torch.uint8, device=device)
+
+
+def rb_filter_batch(descs, bases, blocks, capacity=1 << 22, ws=None, trig=None):
+    """Every block through the hierarchical filter in one call; returns (trigger buffer, count)."""
+    ws = batch_workspace(descs) if ws is None else ws
+    trig = torch.empty(max(capacity, 1) * 24, dtype=torch.uint8, device=ws.device) if trig is None else trig
+    d, b = _pairs(descs, bases)
+    arr = _blocks(descs, blocks)
+    n = C.c_int64(0)
+    rc = _lib().rb_filter_batch(d, b, len(descs), arr, len(blocks), _p(trig), int(capacity), C.byref(n), _p(ws),
+                                ws.numel(), _stream())
+    N.check("rb_filter_batch", rc)
+    return trig, n.value
+
+
+class Batch:
+    """A batch recorded as one CUDA graph (rb_batch_create); run() replays it with one graph
+    launch. Holds references to every device buffer the graph uses."""
+
+    def __init__(self, descs, bases, blocks, capacity=1 << 22, ws=None, trig=None):
+        self.ws = batch_workspace(descs) if ws is None else ws
+        self.trig = torch.empty(max(capacity, 1) * 24, dtype=torch.uint8, device=self.ws.device) if trig is None else trig
+        self.capacity = int(capacity)
+        self._keep = (list(descs), list(bases), list(blocks))
+        d, b = _pairs(descs, bases)
+        arr = _blocks(descs, blocks)
+        h = C.c_void_p()
+        rc = _lib().rb_batch_create(d, b, len(descs), arr, len(blocks), _p(self.trig), self.capacity, _p(self.ws),
+                                    self.ws.numel(), C.byref(h))
+        N.check("rb_batch_create", rc)
+        self._h = h
+
+    def run(self):
+        """Replays the graph on the current stream; returns (trigger buffer, count)."""
+        n = C.c_int64(0)
+        N.check("rb_batch_run", _lib().rb_batch_run(self._h, C.byref(n), _stream()))
+        return self.trig, n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.check("rb_batch_destroy", _lib().rb_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def triggers_numpy(buf: torch.Tensor, n: int) -> np.ndarray:
     """Device trigger buffer -> numpy structured array sorted by (tmpl, sample)."""
     a = _as_np(buf, n, TRIGGER_NP)
@@ -319,6 +413,22 @@ def rb_tune_stage1(desc, basis: Basis, beta_avg: torch.Tensor, ws=None):
                                _stream())
     N.check("rb_tune_stage1", rc)
     return chosen.value, list(times)
+
+
+def rb_tune_fft(desc, basis: Basis, s_hat: torch.Tensor, ws=None):
+    """Times every FFT schedule variant of the basis filter; returns (chosen, ms per variant)."""
+    ws = workspace(desc) if ws is None else ws
+    times = (C.c_double * N.RB_FFT_VARIANTS)()
+    chosen = C.c_int32(-1)
+    b = basis.c_struct()
+    rc = _lib().rb_tune_fft(C.byref(desc), C.byref(b), _p(s_hat), times, C.byref(chosen), _p(ws), ws.numel(),
+                            _stream())
+    N.check("rb_tune_fft", rc)
+    return chosen.value, list(times)
+
+
+def rb_set_fft_variant(desc, variant: int):
+    N.check("rb_set_fft_variant", _lib().rb_set_fft_variant(C.byref(desc), int(variant)))
 
 
 def rb_set_stage1_variant(desc, variant: int):

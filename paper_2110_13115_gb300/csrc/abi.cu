@@ -9,7 +9,9 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include <algorithm>
 #include <atomic>
+#include <memory>
 #include <vector>
 
 namespace {
@@ -143,7 +145,7 @@ void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws
   ws->wt = (float*)take(sizeof(float) * half);
   ws->shat = (float2*)take(sizeof(float2) * half);
   const int64_t nvec = plain ? d.n_templates : d.k;
-  int64_t vc = (int64_t(32) << 20) / (g.n * 8);
+  int64_t vc = (int64_t(64) << 20) / (g.n * 8);  // four-step chunks of up to 64 MB (kept in L2)
   vc = std::max<int64_t>(1, std::min<int64_t>(vc, std::min<int64_t>(nvec, 65535)));
   ws->vc = (int)vc;
   ws->X = (float2*)take(sizeof(float2) * g.n * vc);
@@ -215,7 +217,155 @@ int check_basis(const rb_filter_desc& d, const rb_basis* b, bool need_op = false
   return RB_OK;
 }
 
+int run_stage1(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
+                      const float2* bavg, rb_candidate* cand, cudaStream_t st, StageMarks* mk = nullptr) {
+  if (d.precision == RB_PREC_FP32) {
+    if (mk) mk->to(RB_STAGE_FIRST);
+    return stage1_simt(d, b, g, ws, bavg, cand, st);
+  }
+  if (!b.coeff_op || b.coeff_op_precision != d.precision) {
+    set_detail("coeff_op missing or packed for precision %d (need %d)", b.coeff_op_precision, d.precision);
+    return RB_ERR_BAD_INPUT;
+  }
+  int rc = pack_beta(d, g, bavg, ws.bop_hi, ws.bop_lo, st);
+  if (rc) return rc;
+  if (mk) mk->to(RB_STAGE_FIRST);
+  return stage1_tc(d, b, g, ws, cand, st);
+}
+
+// ---------------------------------------------------------------------------------------
+// Batching: a validated copy of the work list, its enqueue (no host synchronisation, so that it
+// can be recorded as a CUDA graph) and the final status read.
+struct BatchSpec {
+  std::vector<rb_filter_desc> descs;
+  std::vector<rb_basis> bases;
+  std::vector<Geometry> geos;
+  std::vector<rb_block> blocks;
+  rb_trigger* trig = nullptr;
+  int64_t capacity = 0;
+  char* workspace = nullptr;
+};
+
+int batch_workspace(const rb_filter_desc* descs, int32_t n, std::vector<Geometry>* geos, size_t* bytes) {
+  *bytes = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    Geometry g;
+    int rc = make_geometry(descs[i], &g);
+    if (rc) return rc;
+    Workspace w;
+    carve(descs[i], g, nullptr, &w, false);
+    *bytes = std::max(*bytes, w.total);
+    if (geos) geos->push_back(g);
+  }
+  return RB_OK;
+}
+
+int batch_validate(const rb_filter_desc* descs, const rb_basis* bases, int32_t n_bases, const rb_block* blocks,
+                   int64_t n_blocks, rb_trigger* trig, int64_t capacity, void* workspace, size_t bytes,
+                   BatchSpec* out) {
+  if (!descs || !bases || n_bases < 1 || n_blocks < 0 || (n_blocks > 0 && !blocks) || capacity < 0 ||
+      (capacity > 0 && !trig)) {
+    set_detail("NULL array or bad count");
+    return RB_ERR_BAD_INPUT;
+  }
+  size_t need = 0;
+  int rc = batch_workspace(descs, n_bases, &out->geos, &need);
+  if (rc) return rc;
+  for (int32_t i = 0; i < n_bases; ++i) {
+    if ((rc = check_basis(descs[i], &bases[i], true))) return rc;
+    if (bases[i].coeff_op_precision != descs[i].precision) {
+      set_detail("bases[%d] was packed for precision %d, descs[%d] asks for %d", i, bases[i].coeff_op_precision, i,
+                 descs[i].precision);
+      return RB_ERR_BAD_INPUT;
+    }
+  }
+  if (!workspace || bytes < need || ((uintptr_t)workspace & 255)) {
+    set_detail("workspace %p of %zu bytes; need %zu bytes, 256-byte aligned", workspace, bytes, need);
+    return RB_ERR_OOM;
+  }
+  for (int64_t i = 0; i < n_blocks; ++i) {
+    const rb_block& b = blocks[i];
+    if (b.basis < 0 || b.basis >= n_bases || !b.strain || !b.psd) {
+      set_detail("blocks[%lld]: basis index %d (of %d) or NULL strain / psd", (long long)i, b.basis, n_bases);
+      return RB_ERR_BAD_INPUT;
+    }
+    const rb_filter_desc& d = descs[b.basis];
+    if (b.valid_lo < d.n / 2 || b.valid_lo >= d.n || b.valid_lo % d.w) {
+      set_detail("blocks[%lld]: valid_lo %lld must lie in [n/2, n) and be a multiple of w", (long long)i,
+                 (long long)b.valid_lo);
+      return RB_ERR_BAD_INPUT;
+    }
+  }
+  out->descs.assign(descs, descs + n_bases);
+  out->bases.assign(bases, bases + n_bases);
+  out->blocks.assign(blocks, blocks + n_blocks);
+  out->trig = trig;
+  out->capacity = capacity;
+  out->workspace = (char*)workspace;
+  return RB_OK;
+}
+
+// Every block runs the rb_filter pipeline through the one workspace; the status block (flags and
+// counters, the first 256 bytes of every carving) is cleared once, so triggers of all blocks share
+// one counter and the flags are sticky. Only the candidate count is reset per block.
+int batch_enqueue(const BatchSpec& s, cudaStream_t st) {
+  Workspace ws0;
+  carve(s.descs[0], s.geos[0], s.workspace, &ws0, false);
+  RB_CUDA_TRY(cudaMemsetAsync(ws0.flags, 0, 256, st));
+  for (const rb_block& blk : s.blocks) {
+    rb_filter_desc d = s.descs[blk.basis];
+    d.sample_offset = blk.sample_offset;
+    d.block_id = blk.block_id;
+    const Geometry& g = s.geos[blk.basis];
+    const rb_basis& b = s.bases[blk.basis];
+    Workspace ws;
+    carve(d, g, s.workspace, &ws, false);
+    RB_CUDA_TRY(cudaMemsetAsync(ws.cand_count, 0, sizeof(unsigned long long), st));
+    int rc;
+    if ((rc = init_tables(g, ws, blk.psd, d.fs, st))) return rc;
+    if ((rc = whiten(g, ws, blk.strain, ws.shat, st))) return rc;
+    if ((rc = bank_filter(g, ws, (const float2*)b.vectors, d.k, ws.shat, ws.beta, ws.bavg, d.w, st))) return rc;
+    if ((rc = run_stage1(d, b, g, ws, ws.bavg, ws.cand, st))) return rc;
+    const int bin_lo = (int)((blk.valid_lo - d.n / 2) / d.w);
+    if ((rc = stage2_bucketed(d, b, g, ws, ws.beta, s.trig, s.capacity, ws.trig_count, bin_lo, st))) return rc;
+  }
+  return RB_OK;
+}
+
+int batch_status(const BatchSpec& s, int64_t* n_trig, cudaStream_t st) {
+  Workspace ws0;
+  carve(s.descs[0], s.geos[0], s.workspace, &ws0, false);
+  Status stt;
+  int rc = read_status(ws0, &stt, st);
+  if (rc) return rc;
+  *n_trig = (int64_t)stt.trig;
+  if (stt.flags & RB_FLAG_BAD_PSD) {
+    set_detail("a block's PSD is not finite and positive on 0 < j < n/2");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (stt.flags & RB_FLAG_TIMEOUT) {
+    set_detail("a device-side wait of the first stage timed out");
+    return RB_ERR_TIMEOUT;
+  }
+  if (stt.flags & RB_FLAG_CAND_OVERFLOW) {
+    set_detail("a block had more first-stage candidates than its desc's cand_capacity");
+    return RB_ERR_OVERFLOW;
+  }
+  if ((int64_t)stt.trig > s.capacity) {
+    set_detail("%llu triggers exceed capacity %lld", stt.trig, (long long)s.capacity);
+    return RB_ERR_OVERFLOW;
+  }
+  return RB_OK;
+}
+
 }  // namespace
+
+struct rb_batch {
+  BatchSpec spec;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t launches = 0;  // kernels recorded in the graph
+};
 
 extern "C" {
 
@@ -342,21 +492,6 @@ int rb_pack_coeff(const rb_filter_desc* desc, const rb_basis* basis, void* out, 
   return pack_coeff(*desc, *basis, g, out, (cudaStream_t)stream);
 }
 
-static int run_stage1(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-                      const float2* bavg, rb_candidate* cand, cudaStream_t st, StageMarks* mk = nullptr) {
-  if (d.precision == RB_PREC_FP32) {
-    if (mk) mk->to(RB_STAGE_FIRST);
-    return stage1_simt(d, b, g, ws, bavg, cand, st);
-  }
-  if (!b.coeff_op || b.coeff_op_precision != d.precision) {
-    set_detail("coeff_op missing or packed for precision %d (need %d)", b.coeff_op_precision, d.precision);
-    return RB_ERR_BAD_INPUT;
-  }
-  int rc = pack_beta(d, g, bavg, ws.bop_hi, ws.bop_lo, st);
-  if (rc) return rc;
-  if (mk) mk->to(RB_STAGE_FIRST);
-  return stage1_tc(d, b, g, ws, cand, st);
-}
 
 int rb_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* beta_avg, rb_candidate* cand,
               int64_t* n_cand, void* workspace, size_t workspace_bytes, void* stream) {
@@ -390,6 +525,39 @@ int rb_set_stage1_variant(const rb_filter_desc* desc, int32_t variant) {
   int rc = make_geometry(*desc, &g);
   if (rc) return rc;
   return set_stage1_variant(*desc, g, variant);
+}
+
+int rb_set_fft_variant(const rb_filter_desc* desc, int32_t variant) {
+  if (!desc) {
+    set_detail("desc is NULL");
+    return RB_ERR_BAD_INPUT;
+  }
+  Geometry g;
+  int rc = make_geometry(*desc, &g);
+  if (rc) return rc;
+  return set_fft_variant(g, desc->w, variant);
+}
+
+int rb_tune_fft(const rb_filter_desc* desc, const rb_basis* basis, const float* s_hat, double* times_ms,
+                int32_t* chosen, void* workspace, size_t workspace_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Geometry g;
+  Workspace ws;
+  int rc = prepare(desc, workspace, workspace_bytes, false, &g, &ws, st);
+  if (rc) return rc;
+  if ((rc = check_basis(*desc, basis))) return rc;
+  if (!s_hat || !times_ms || !chosen) {
+    set_detail("NULL argument");
+    return RB_ERR_BAD_INPUT;
+  }
+  if ((rc = init_tables(g, ws, nullptr, desc->fs, st))) return rc;
+  for (int v = 0; v < RB_FFT_VARIANTS; ++v) times_ms[v] = -1.0;
+  int best = 0;
+  if ((rc = tune_fft(g, ws, (const float2*)basis->vectors, desc->k, (const float2*)s_hat, ws.beta, ws.bavg,
+                     desc->w, times_ms, &best, st)))
+    return rc;
+  *chosen = best;
+  return RB_OK;
 }
 
 int rb_tune_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* beta_avg, double* times_ms,
@@ -438,7 +606,7 @@ int rb_stage2(const rb_filter_desc* desc, const rb_basis* basis, const float* be
     RB_CUDA_TRY(cudaMemcpyAsync(ws.cand, cand, sizeof(rb_candidate) * n_cand, cudaMemcpyDeviceToDevice, st));
     RB_CUDA_TRY(cudaMemcpyAsync(ws.cand_count, &cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
     RB_CUDA_TRY(cudaStreamSynchronize(st));  // cnt lives on this stack frame
-    if ((rc = stage2_bucketed(*desc, *basis, g, ws, (const float2*)beta, trig, capacity, st))) return rc;
+    if ((rc = stage2_bucketed(*desc, *basis, g, ws, (const float2*)beta, trig, capacity, ws.trig_count, 0, st))) return rc;
   }
   Status s;
   if ((rc = read_status(ws, &s, st))) return rc;
@@ -470,7 +638,7 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
   mk.to(RB_STAGE_PACK);
   if ((rc = run_stage1(*desc, *basis, g, ws, ws.bavg, ws.cand, st, &mk))) return rc;
   mk.to(RB_STAGE_SECOND);
-  if ((rc = stage2_bucketed(*desc, *basis, g, ws, ws.beta, trig, capacity, st))) return rc;
+  if ((rc = stage2_bucketed(*desc, *basis, g, ws, ws.beta, trig, capacity, ws.trig_count, 0, st))) return rc;
   mk.finish();
   Status s;
   if ((rc = read_status(ws, &s, st))) return rc;
@@ -524,6 +692,99 @@ int rb_filter_plain(const rb_filter_desc* desc, const float* templates, const fl
     return RB_ERR_OVERFLOW;
   }
   return RB_OK;
+}
+
+int rb_batch_plan(const rb_filter_desc* descs, int32_t n_descs, size_t* workspace_bytes) {
+  if (!descs || n_descs < 1 || !workspace_bytes) {
+    set_detail("NULL argument or n_descs < 1");
+    return RB_ERR_BAD_INPUT;
+  }
+  return batch_workspace(descs, n_descs, nullptr, workspace_bytes);
+}
+
+int rb_filter_batch(const rb_filter_desc* descs, const rb_basis* bases, int32_t n_bases, const rb_block* blocks,
+                    int64_t n_blocks, rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* workspace,
+                    size_t workspace_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!n_trig) {
+    set_detail("n_trig is NULL");
+    return RB_ERR_BAD_INPUT;
+  }
+  BatchSpec spec;
+  int rc = batch_validate(descs, bases, n_bases, blocks, n_blocks, trig, capacity, workspace, workspace_bytes, &spec);
+  if (rc) return rc;
+  if ((rc = batch_enqueue(spec, st))) return rc;
+  return batch_status(spec, n_trig, st);
+}
+
+int rb_batch_create(const rb_filter_desc* descs, const rb_basis* bases, int32_t n_bases, const rb_block* blocks,
+                    int64_t n_blocks, rb_trigger* trig, int64_t capacity, void* workspace, size_t workspace_bytes,
+                    rb_batch** out) {
+  if (!out) {
+    set_detail("out is NULL");
+    return RB_ERR_BAD_INPUT;
+  }
+  *out = nullptr;
+  std::unique_ptr<rb_batch> bt(new rb_batch);
+  int rc = batch_validate(descs, bases, n_bases, blocks, n_blocks, trig, capacity, workspace, workspace_bytes,
+                          &bt->spec);
+  if (rc) return rc;
+  // record on a private stream (the caller's may be the legacy default stream, which cannot capture)
+  cudaStream_t cs = nullptr;
+  RB_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const uint64_t l0 = g_launches.load();
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    set_detail("cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    return RB_ERR_CUDA;
+  }
+  rc = batch_enqueue(bt->spec, cs);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  cudaStreamDestroy(cs);
+  const uint64_t recorded = g_launches.load() - l0;
+  g_launches.fetch_sub(recorded);  // recorded, not launched: counted at each run
+  if (rc == RB_OK && (e != cudaSuccess || !graph)) {
+    set_detail("stream capture failed: %s", cudaGetErrorString(e));
+    rc = RB_ERR_CUDA;
+  }
+  if (rc == RB_OK) {
+    e = cudaGraphInstantiate(&bt->exec, graph, 0);
+    if (e != cudaSuccess) {
+      set_detail("cudaGraphInstantiate: %s", cudaGetErrorString(e));
+      rc = RB_ERR_CUDA;
+    }
+  }
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc;
+  }
+  bt->graph = graph;
+  bt->launches = recorded;
+  *out = bt.release();
+  return RB_OK;
+}
+
+int rb_batch_run(rb_batch* batch, int64_t* n_trig, void* stream) {
+  if (!batch || !n_trig) {
+    set_detail("NULL argument");
+    return RB_ERR_BAD_INPUT;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  RB_CUDA_TRY(cudaGraphLaunch(batch->exec, st));
+  g_launches.fetch_add(batch->launches);
+  return batch_status(batch->spec, n_trig, st);
+}
+
+int rb_batch_destroy(rb_batch* batch) {
+  if (!batch) return RB_OK;
+  int rc = RB_OK;
+  if (batch->exec && cudaGraphExecDestroy(batch->exec) != cudaSuccess) rc = RB_ERR_CUDA;
+  if (batch->graph && cudaGraphDestroy(batch->graph) != cudaSuccess) rc = RB_ERR_CUDA;
+  delete batch;
+  return rc;
 }
 
 }  // extern "C"

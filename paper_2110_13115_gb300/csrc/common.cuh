@@ -29,7 +29,7 @@ void rb_count_launch();
 void rb_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
 // Device status words (in workspace): bad input, overflow counters.
-enum { RB_FLAG_BAD_PSD = 1, RB_FLAG_BAD_STRAIN = 2, RB_FLAG_TIMEOUT = 4 };
+enum { RB_FLAG_BAD_PSD = 1, RB_FLAG_BAD_STRAIN = 2, RB_FLAG_TIMEOUT = 4, RB_FLAG_CAND_OVERFLOW = 8 };
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

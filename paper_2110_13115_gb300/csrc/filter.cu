@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 
@@ -122,7 +124,7 @@ constexpr int pass_a_smem_bytes() {
 }
 
 // ---------------------------------------------------------------------------------------
-// Pass B: 16 columns m2 of length L = n1, input X[vec][j1][m2]; output sample
+// Pass B: G columns m2 of length L = n1, input X[vec][j1][m2]; output sample
 // m = m2 + n2 m1 of the long transform.
 //  MODE_BANK  : keep m in [n/2, n): beta[vec][m - n/2] and the W-sample bin means
 //               beta_avg[vec][(m - n/2)/W] (Eq. 9).
@@ -145,9 +147,9 @@ struct PassBArgs {
   int block_id;
 };
 
-template <int MODE, int L, int W>
-__global__ void __launch_bounds__(L) k_pass_b(PassBArgs a, const float2* __restrict__ tab_n1) {
-  constexpr int G = 16;
+template <int MODE, int L, int W, int G>
+__global__ void __launch_bounds__(G * L / kE) k_pass_b(PassBArgs a, const float2* __restrict__ tab_n1) {
+  static_assert(G >= W, "a bin's W columns must lie in one CTA");
   constexpr int SIGN = MODE == MODE_STRAIN ? -1 : 1;
   extern __shared__ float2 smem[];
   float2* tw = smem;
@@ -218,9 +220,9 @@ __global__ void __launch_bounds__(L) k_pass_b(PassBArgs a, const float2* __restr
     }
 }
 
-template <int L>
+template <int L, int G>
 constexpr int pass_b_smem_bytes() {
-  return (L + Smem<L, 16>::data) * 8;
+  return (L + Smem<L, G>::data) * 8;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -398,15 +400,16 @@ static cudaError_t allow_smem(K kernel, int bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+// Columns per CTA of the four-step passes. Inner (pass A) and outer (pass B) lengths of 256 and
+// more take the tuned variant's widths; shorter lengths use fixed widths that keep CTAs >= 64 threads.
 template <int L>
 struct GA {
   static constexpr int value = L >= 512 ? 8 : (L >= 128 ? 16 : 32);
 };
 
-template <int MODE, int L>
-static int launch_a_L(const rb::Geometry& g, const float2* rows, const float2* shat, const float* strain,
-                      float2* X, const rb::Tables& tb, int64_t vec0, int nvec, cudaStream_t st) {
-  constexpr int G = GA<L>::value;
+template <int MODE, int L, int G>
+static int launch_a_LG(const rb::Geometry& g, const float2* rows, const float2* shat, const float* strain,
+                       float2* X, const rb::Tables& tb, int64_t vec0, int nvec, cudaStream_t st) {
   constexpr int smem = pass_a_smem_bytes<L, G>();
   auto kern = k_pass_a<MODE, L, G>;
   RB_CUDA_TRY(allow_smem(kern, smem));
@@ -416,61 +419,101 @@ static int launch_a_L(const rb::Geometry& g, const float2* rows, const float2* s
   return RB_OK;
 }
 
+template <int MODE, int L>
+static int launch_a_L(const rb::Geometry& g, const float2* rows, const float2* shat, const float* strain,
+                      float2* X, const rb::Tables& tb, int64_t vec0, int nvec, int ga, cudaStream_t st) {
+  if constexpr (L >= 256) {
+    if (ga == 4 && g.n1 >= 4) return launch_a_LG<MODE, L, 4>(g, rows, shat, strain, X, tb, vec0, nvec, st);
+    if (ga == 16 && g.n1 >= 16) return launch_a_LG<MODE, L, 16>(g, rows, shat, strain, X, tb, vec0, nvec, st);
+  }
+  return launch_a_LG<MODE, L, GA<L>::value>(g, rows, shat, strain, X, tb, vec0, nvec, st);
+}
+
 template <int MODE>
 static int launch_a(const rb::Geometry& g, const float2* rows, const float2* shat, const float* strain,
-                    float2* X, const rb::Tables& tb, int64_t vec0, int nvec, cudaStream_t st) {
+                    float2* X, const rb::Tables& tb, int64_t vec0, int nvec, int ga, cudaStream_t st) {
   switch (g.n2) {
-    case 32: return launch_a_L<MODE, 32>(g, rows, shat, strain, X, tb, vec0, nvec, st);
-    case 64: return launch_a_L<MODE, 64>(g, rows, shat, strain, X, tb, vec0, nvec, st);
-    case 128: return launch_a_L<MODE, 128>(g, rows, shat, strain, X, tb, vec0, nvec, st);
-    case 256: return launch_a_L<MODE, 256>(g, rows, shat, strain, X, tb, vec0, nvec, st);
-    case 512: return launch_a_L<MODE, 512>(g, rows, shat, strain, X, tb, vec0, nvec, st);
-    case 1024: return launch_a_L<MODE, 1024>(g, rows, shat, strain, X, tb, vec0, nvec, st);
+    case 32: return launch_a_L<MODE, 32>(g, rows, shat, strain, X, tb, vec0, nvec, ga, st);
+    case 64: return launch_a_L<MODE, 64>(g, rows, shat, strain, X, tb, vec0, nvec, ga, st);
+    case 128: return launch_a_L<MODE, 128>(g, rows, shat, strain, X, tb, vec0, nvec, ga, st);
+    case 256: return launch_a_L<MODE, 256>(g, rows, shat, strain, X, tb, vec0, nvec, ga, st);
+    case 512: return launch_a_L<MODE, 512>(g, rows, shat, strain, X, tb, vec0, nvec, ga, st);
+    case 1024: return launch_a_L<MODE, 1024>(g, rows, shat, strain, X, tb, vec0, nvec, ga, st);
   }
   rb::set_detail("unsupported inner FFT length %d", g.n2);
   return RB_ERR_UNSUPPORTED;
 }
 
-template <int MODE, int L, int W>
-static int launch_b_LW(const rb::Geometry& g, const PassBArgs& a, const rb::Tables& tb, int nvec,
-                       cudaStream_t st) {
-  constexpr int smem = pass_b_smem_bytes<L>();
-  auto kern = k_pass_b<MODE, L, W>;
+template <int MODE, int L, int W, int G>
+static int launch_b_LWG(const rb::Geometry& g, const PassBArgs& a, const rb::Tables& tb, int nvec,
+                        cudaStream_t st) {
+  constexpr int smem = pass_b_smem_bytes<L, G>();
+  auto kern = k_pass_b<MODE, L, W, G>;
   RB_CUDA_TRY(allow_smem(kern, smem));
-  dim3 grid(g.n2 / 16, nvec);
-  kern<<<grid, L, smem, st>>>(a, tb.n1);
+  dim3 grid(g.n2 / G, nvec);
+  kern<<<grid, G * L / kE, smem, st>>>(a, tb.n1);
   RB_LAUNCH_CHECK();
   return RB_OK;
 }
 
+template <int MODE, int L, int W>
+static int launch_b_LW(const rb::Geometry& g, const PassBArgs& a, const rb::Tables& tb, int nvec, int gb,
+                       cudaStream_t st) {
+  if constexpr (L >= 256 && W <= 8 && MODE != MODE_STRAIN)
+    if (gb == 8) return launch_b_LWG<MODE, L, W, 8>(g, a, tb, nvec, st);
+  return launch_b_LWG<MODE, L, W, 16>(g, a, tb, nvec, st);
+}
+
 template <int MODE, int L>
-static int launch_b_L(const rb::Geometry& g, const PassBArgs& a, const rb::Tables& tb, int nvec, int w,
+static int launch_b_L(const rb::Geometry& g, const PassBArgs& a, const rb::Tables& tb, int nvec, int w, int gb,
                       cudaStream_t st) {
-  if constexpr (MODE == MODE_STRAIN) return launch_b_LW<MODE, L, 1>(g, a, tb, nvec, st);
+  if constexpr (MODE == MODE_STRAIN) return launch_b_LW<MODE, L, 1>(g, a, tb, nvec, gb, st);
   switch (w) {
-    case 1: return launch_b_LW<MODE, L, 1>(g, a, tb, nvec, st);
-    case 2: return launch_b_LW<MODE, L, 2>(g, a, tb, nvec, st);
-    case 4: return launch_b_LW<MODE, L, 4>(g, a, tb, nvec, st);
-    case 8: return launch_b_LW<MODE, L, 8>(g, a, tb, nvec, st);
-    case 16: return launch_b_LW<MODE, L, 16>(g, a, tb, nvec, st);
+    case 1: return launch_b_LW<MODE, L, 1>(g, a, tb, nvec, gb, st);
+    case 2: return launch_b_LW<MODE, L, 2>(g, a, tb, nvec, gb, st);
+    case 4: return launch_b_LW<MODE, L, 4>(g, a, tb, nvec, gb, st);
+    case 8: return launch_b_LW<MODE, L, 8>(g, a, tb, nvec, gb, st);
+    case 16: return launch_b_LW<MODE, L, 16>(g, a, tb, nvec, gb, st);
   }
   rb::set_detail("unsupported bin width %d", w);
   return RB_ERR_BAD_INPUT;
 }
 
 template <int MODE>
-static int launch_b(const rb::Geometry& g, const PassBArgs& a, const rb::Tables& tb, int nvec, int w,
+static int launch_b(const rb::Geometry& g, const PassBArgs& a, const rb::Tables& tb, int nvec, int w, int gb,
                     cudaStream_t st) {
   switch (g.n1) {
-    case 32: return launch_b_L<MODE, 32>(g, a, tb, nvec, w, st);
-    case 64: return launch_b_L<MODE, 64>(g, a, tb, nvec, w, st);
-    case 128: return launch_b_L<MODE, 128>(g, a, tb, nvec, w, st);
-    case 256: return launch_b_L<MODE, 256>(g, a, tb, nvec, w, st);
-    case 512: return launch_b_L<MODE, 512>(g, a, tb, nvec, w, st);
-    case 1024: return launch_b_L<MODE, 1024>(g, a, tb, nvec, w, st);
+    case 32: return launch_b_L<MODE, 32>(g, a, tb, nvec, w, gb, st);
+    case 64: return launch_b_L<MODE, 64>(g, a, tb, nvec, w, gb, st);
+    case 128: return launch_b_L<MODE, 128>(g, a, tb, nvec, w, gb, st);
+    case 256: return launch_b_L<MODE, 256>(g, a, tb, nvec, w, gb, st);
+    case 512: return launch_b_L<MODE, 512>(g, a, tb, nvec, w, gb, st);
+    case 1024: return launch_b_L<MODE, 1024>(g, a, tb, nvec, w, gb, st);
   }
   rb::set_detail("unsupported outer FFT length %d", g.n1);
   return RB_ERR_UNSUPPORTED;
+}
+
+// FFT schedule variants of the basis filter: columns per CTA of pass A and pass B, and the size
+// in MB of a four-step chunk's intermediate X (which stays in L2 between the passes).
+struct FftVariant {
+  int ga, gb, mb;
+};
+constexpr FftVariant kFftVariants[RB_FFT_VARIANTS] = {{8, 16, 32}, {4, 8, 32}, {4, 16, 32}, {8, 8, 32},
+                                                      {4, 8, 64}, {8, 16, 64}};
+
+int chunk_vectors(const rb::Geometry& g, const rb::Workspace& ws, const FftVariant& v) {
+  const int64_t want = ((int64_t)v.mb << 20) / (g.n * 8);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, ws.vc));
+}
+
+std::mutex g_fft_mu;
+std::map<std::pair<int64_t, int>, int> g_fft_choice;  // (n, w) -> variant
+
+int fft_variant_for(int64_t n, int w) {
+  std::lock_guard<std::mutex> lk(g_fft_mu);
+  auto it = g_fft_choice.find({n, w});
+  return it == g_fft_choice.end() ? 0 : it->second;
 }
 
 }  // namespace
@@ -491,21 +534,22 @@ int init_tables(const Geometry& g, const Workspace& ws, const double* psd, doubl
 }
 
 int whiten(const Geometry& g, const Workspace& ws, const float* strain, float2* shat, cudaStream_t st) {
-  int rc = launch_a<MODE_STRAIN>(g, nullptr, nullptr, strain, ws.X, ws.tables, 0, 1, st);
+  int rc = launch_a<MODE_STRAIN>(g, nullptr, nullptr, strain, ws.X, ws.tables, 0, 1, 8, st);
   if (rc) return rc;
   PassBArgs a{};
   a.X = ws.X;
   a.n2 = g.n2;
   a.shat = shat;
   a.wt = ws.wt;
-  return launch_b<MODE_STRAIN>(g, a, ws.tables, 1, 1, st);
+  return launch_b<MODE_STRAIN>(g, a, ws.tables, 1, 1, 16, st);
 }
 
-int bank_filter(const Geometry& g, const Workspace& ws, const float2* rows, int64_t nvec, const float2* shat,
-                float2* beta, float2* bavg, int w, cudaStream_t st) {
-  for (int64_t v0 = 0; v0 < nvec; v0 += ws.vc) {
-    const int cnt = (int)std::min<int64_t>(ws.vc, nvec - v0);
-    int rc = launch_a<MODE_BANK>(g, rows, shat, nullptr, ws.X, ws.tables, v0, cnt, st);
+static int bank_filter_v(const Geometry& g, const Workspace& ws, const float2* rows, int64_t nvec,
+                         const float2* shat, float2* beta, float2* bavg, int w, const FftVariant& v, cudaStream_t st) {
+  const int vc = chunk_vectors(g, ws, v);
+  for (int64_t v0 = 0; v0 < nvec; v0 += vc) {
+    const int cnt = (int)std::min<int64_t>(vc, nvec - v0);
+    int rc = launch_a<MODE_BANK>(g, rows, shat, nullptr, ws.X, ws.tables, v0, cnt, v.ga, st);
     if (rc) return rc;
     PassBArgs a{};
     a.X = ws.X;
@@ -513,18 +557,66 @@ int bank_filter(const Geometry& g, const Workspace& ws, const float2* rows, int6
     a.vec0 = v0;
     a.beta = beta;
     a.beta_avg = bavg;
-    rc = launch_b<MODE_BANK>(g, a, ws.tables, cnt, w, st);
+    rc = launch_b<MODE_BANK>(g, a, ws.tables, cnt, w, v.gb, st);
     if (rc) return rc;
   }
   return RB_OK;
 }
 
+int bank_filter(const Geometry& g, const Workspace& ws, const float2* rows, int64_t nvec, const float2* shat,
+                float2* beta, float2* bavg, int w, cudaStream_t st) {
+  return bank_filter_v(g, ws, rows, nvec, shat, beta, bavg, w, kFftVariants[fft_variant_for(g.n, w)], st);
+}
+
+int set_fft_variant(const Geometry& g, int w, int variant) {
+  if (variant < 0 || variant >= RB_FFT_VARIANTS) {
+    set_detail("FFT variant %d outside [0, %d)", variant, RB_FFT_VARIANTS);
+    return RB_ERR_BAD_INPUT;
+  }
+  std::lock_guard<std::mutex> lk(g_fft_mu);
+  g_fft_choice[{g.n, w}] = variant;
+  return RB_OK;
+}
+
+int tune_fft(const Geometry& g, const Workspace& ws, const float2* rows, int64_t nvec, const float2* shat,
+             float2* beta, float2* bavg, int w, double* ms, int* chosen, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  RB_CUDA_TRY(cudaEventCreate(&e0));
+  RB_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = RB_OK, best = 0;
+  for (int v = 0; v < RB_FFT_VARIANTS && rc == RB_OK; ++v) {
+    const int reps = 3;
+    rc = bank_filter_v(g, ws, rows, nvec, shat, beta, bavg, w, kFftVariants[v], st);  // warm-up
+    if (rc == RB_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = RB_ERR_CUDA;
+    for (int r = 0; r < reps && rc == RB_OK; ++r)
+      rc = bank_filter_v(g, ws, rows, nvec, shat, beta, bavg, w, kFftVariants[v], st);
+    float t = 0.f;
+    if (rc == RB_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+      rc = RB_ERR_CUDA;
+    if (rc == RB_OK) {
+      ms[v] = t / reps;
+      if (ms[v] < ms[best]) best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    if (rc == RB_ERR_CUDA) set_detail("FFT tuning timing failed");
+    return rc;
+  }
+  *chosen = best;
+  return set_fft_variant(g, w, best);
+}
+
 int plain_filter(const Geometry& g, const Workspace& ws, const float2* tmpl, int64_t T, const float2* shat,
                  int w, float thr2, int64_t sample_offset, int block_id, rb_trigger* trig, int64_t cap,
                  cudaStream_t st) {
-  for (int64_t v0 = 0; v0 < T; v0 += ws.vc) {
-    const int cnt = (int)std::min<int64_t>(ws.vc, T - v0);
-    int rc = launch_a<MODE_BANK>(g, tmpl, shat, nullptr, ws.X, ws.tables, v0, cnt, st);
+  const FftVariant& v = kFftVariants[fft_variant_for(g.n, w)];
+  const int vc = chunk_vectors(g, ws, v);
+  for (int64_t v0 = 0; v0 < T; v0 += vc) {
+    const int cnt = (int)std::min<int64_t>(vc, T - v0);
+    int rc = launch_a<MODE_BANK>(g, tmpl, shat, nullptr, ws.X, ws.tables, v0, cnt, v.ga, st);
     if (rc) return rc;
     PassBArgs a{};
     a.X = ws.X;
@@ -536,7 +628,7 @@ int plain_filter(const Geometry& g, const Workspace& ws, const float2* tmpl, int
     a.thr2 = thr2;
     a.sample_offset = sample_offset;
     a.block_id = block_id;
-    rc = launch_b<MODE_PLAIN>(g, a, ws.tables, cnt, w, st);
+    rc = launch_b<MODE_PLAIN>(g, a, ws.tables, cnt, w, v.gb, st);
     if (rc) return rc;
   }
   return RB_OK;

@@ -67,6 +67,10 @@ int bank_filter(const Geometry& g, const Workspace& ws, const float2* rows, int6
 int plain_filter(const Geometry& g, const Workspace& ws, const float2* tmpl, int64_t T, const float2* shat,
                  int w, float thr2, int64_t sample_offset, int block_id, rb_trigger* trig, int64_t cap,
                  cudaStream_t st);
+// FFT schedule variants of the basis filter and the template-method comparator (per n and w)
+int set_fft_variant(const Geometry& g, int w, int variant);
+int tune_fft(const Geometry& g, const Workspace& ws, const float2* rows, int64_t nvec, const float2* shat,
+             float2* beta, float2* bavg, int w, double* ms, int* chosen, cudaStream_t st);
 int stage1_simt(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
                 const float2* bavg, rb_candidate* cand, cudaStream_t st);
 int pack_beta(const rb_filter_desc& d, const Geometry& g, const float2* bavg, void* hi, void* lo,
@@ -78,7 +82,10 @@ int tune_stage1(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, c
                 int* chosen, cudaStream_t st);
 int stage1_tc_variants();
 int set_stage1_variant(const rb_filter_desc& d, const Geometry& g, int variant);
+// Second stage on ws.cand (count at ws.cand_count): bucketing by bin, then exact reconstruction;
+// triggers are appended at *counter. Bins before bin_lo (relative to the first valid bin) are skipped.
 int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-                    const float2* beta, rb_trigger* trig, int64_t cap, cudaStream_t st);
+                    const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, int bin_lo,
+                    cudaStream_t st);
 
 }  // namespace rb

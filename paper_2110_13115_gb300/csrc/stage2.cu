@@ -29,15 +29,19 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kPiece = rb::kStage2Piece;  // candidates per second-stage work item
 
 // Per-bin counts; lanes holding the same bin combine into one atomic.
+// Bins before blo (relative to bin0) are dropped: a block whose earlier valid samples another
+// block already covers keeps only [blo, nb).
 __global__ void k_bin_count(const rb_candidate* __restrict__ cand, const unsigned long long* dev_count, int64_t cap,
-                            int bin0, int nb, unsigned* __restrict__ count) {
-  const int64_t n = (int64_t)min((unsigned long long)cap, *dev_count);
+                            int bin0, int blo, int nb, unsigned* __restrict__ count, unsigned* flags) {
+  const unsigned long long found = *dev_count;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && found > (unsigned long long)cap) atomicOr(flags, (unsigned)RB_FLAG_CAND_OVERFLOW);
+  const int64_t n = (int64_t)min((unsigned long long)cap, found);
   const int lane = threadIdx.x & 31;
   for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~int64_t(31); i0 < n;
        i0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = i0 + lane;
     int b = i < n ? cand[i].bin - bin0 : -1;
-    if (b >= nb) b = -1;
+    if (b < blo || b >= nb) b = -1;
     const unsigned peers = __match_any_sync(kFull, b);
     if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(count + b, (unsigned)__popc(peers));
   }
@@ -111,7 +115,8 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
 }
 
 __global__ void k_bin_scatter(const rb_candidate* __restrict__ cand, const unsigned long long* dev_count, int64_t cap,
-                              int bin0, int nb, const unsigned* __restrict__ start, unsigned* __restrict__ cursor,
+                              int bin0, int blo, int nb, const unsigned* __restrict__ start,
+                              unsigned* __restrict__ cursor,
                               rb_candidate* __restrict__ out) {
   const int64_t n = (int64_t)min((unsigned long long)cap, *dev_count);
   const int lane = threadIdx.x & 31;
@@ -123,7 +128,7 @@ __global__ void k_bin_scatter(const rb_candidate* __restrict__ cand, const unsig
     if (i < n) {
       c = cand[i];
       b = c.bin - bin0;
-      if (b >= nb) b = -1;
+      if (b < blo || b >= nb) b = -1;
     }
     const unsigned peers = __match_any_sync(kFull, b);
     const int leader = __ffs(peers) - 1;
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
 
 template <int W>
 int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
-                const float2* beta, rb_trigger* trig, int64_t cap, cudaStream_t st) {
+                const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st) {
   constexpr int NT = S2<W>::NT;
   const int nb = (int)g.n_bins;
   const int k16 = (d.k + 15) / 16 * 16;
@@ -337,7 +342,7 @@ int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& 
   const __half* ahi = reinterpret_cast<const __half*>(b.coeff_op);
   const __half* alo = ahi + (int64_t)d.n_templates * 2 * k16;
   kern<<<grid, 256, smem, st>>>(ahi, alo, beta, d.k, k16, d.n_templates, g.n / 2, nb, ws.pieces, ws.piece_total,
-                                ws.cand_sorted, d.rho_ii * d.rho_ii, d.sample_offset, trig, ws.trig_count, cap);
+                                ws.cand_sorted, d.rho_ii * d.rho_ii, d.sample_offset, trig, counter, cap);
   RB_LAUNCH_CHECK();
   return RB_OK;
 }
@@ -347,23 +352,25 @@ int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& 
 namespace rb {
 
 int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-                    const float2* beta, rb_trigger* trig, int64_t cap, cudaStream_t st) {
+                    const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, int bin_lo,
+                    cudaStream_t st) {
   const int nb = (int)g.n_bins;
   const int bin0 = nb;  // valid bins are [n/(2w), n/w)
   RB_CUDA_TRY(cudaMemsetAsync(ws.bin_count, 0, sizeof(unsigned) * (nb + 1), st));
-  k_bin_count<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, nb, ws.bin_count);
+  k_bin_count<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb,
+                                       ws.bin_count, ws.flags);
   RB_LAUNCH_CHECK();
   k_bin_scan<<<1, 1024, 0, st>>>(ws.bin_count, ws.bin_start, nb, ws.pieces, ws.piece_total);
   RB_LAUNCH_CHECK();
-  k_bin_scatter<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, nb, ws.bin_start,
+  k_bin_scatter<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, ws.bin_start,
                                          ws.bin_count, ws.cand_sorted);
   RB_LAUNCH_CHECK();
   switch (d.w) {
-    case 1: return launch_bins<1>(d, b, g, ws, beta, trig, cap, st);
-    case 2: return launch_bins<2>(d, b, g, ws, beta, trig, cap, st);
-    case 4: return launch_bins<4>(d, b, g, ws, beta, trig, cap, st);
-    case 8: return launch_bins<8>(d, b, g, ws, beta, trig, cap, st);
-    case 16: return launch_bins<16>(d, b, g, ws, beta, trig, cap, st);
+    case 1: return launch_bins<1>(d, b, g, ws, beta, trig, cap, counter, st);
+    case 2: return launch_bins<2>(d, b, g, ws, beta, trig, cap, counter, st);
+    case 4: return launch_bins<4>(d, b, g, ws, beta, trig, cap, counter, st);
+    case 8: return launch_bins<8>(d, b, g, ws, beta, trig, cap, counter, st);
+    case 16: return launch_bins<16>(d, b, g, ws, beta, trig, cap, counter, st);
   }
   return RB_ERR_BAD_INPUT;
 }

@@ -268,6 +268,16 @@ def full(w: int = 8, k: int = 256, n_templates: int = 10000, n_inj: int = 20, se
                          n_inj=n_inj, snr_range=(5.0, 20.0), min_sep=4.0, segment=segment, noise=noise)
 
 
+def precision(k: int = 400, w: int = 8, n_templates: int = 50000, n_inj: int = 3,
+              noise: bool = True) -> Workload:
+    """50,000 templates (masses 1-50, non-spinning, 1.5PN), 128 s at 4096 Hz with f_low = 40 Hz
+    (so the longest template, 43.6 s, fits the 64-s valid half), 3 injections SNR 10-20."""
+    grid = Grid(fs=4096.0, n=524288, f_low=40.0)
+    spec = BankSpec(n_templates, 1.0, 50.0, 0.0, 3)
+    return make_workload(f"precision-{n_templates}x128s@4096Hz", grid, spec, k=k, w=w, rho_ii=5.0,
+                         n_inj=n_inj, snr_range=(10.0, 20.0), min_sep=4.0, noise=noise)
+
+
 def scaled(name: str, fs: float, n: int, n_templates: int, m_range=(3.0, 50.0), chi_max=0.5, pn_order=3,
            f_low=30.0, k=64, w=8, n_inj=2, snr_range=(8.0, 15.0), rho_ii=5.0, min_sep=1.0,
            segment=0, detector=0, psd_scale=1.0) -> Workload:
@@ -276,3 +286,116 @@ def scaled(name: str, fs: float, n: int, n_templates: int, m_range=(3.0, 50.0), 
     spec = BankSpec(n_templates, m_range[0], m_range[1], chi_max, pn_order)
     return make_workload(name, grid, spec, k=k, w=w, rho_ii=rho_ii, n_inj=n_inj, snr_range=snr_range,
                          min_sep=min_sep, segment=segment, detector=detector, psd_scale=psd_scale)
+
+
+# --- batches of uneven segments from two detectors ----------------------------------------
+
+@dataclasses.dataclass
+class Segment:
+    """One detector's strain over one segment (float32, ``length`` samples from ``start``)."""
+
+    index: int
+    detector: int
+    start: int  # global sample index of the segment's first sample
+    strain: np.ndarray
+    psd_scale: float
+    injections: list
+
+
+@dataclasses.dataclass
+class BatchBlock:
+    """A filtering block of a segment: samples [offset, offset + n) of the segment, keeping
+    triggers at block samples >= valid_lo (n/2, or more for a right-aligned tail block)."""
+
+    segment: int  # index into BatchWorkload.segments
+    offset: int
+    n: int
+    valid_lo: int
+
+
+@dataclasses.dataclass
+class BatchWorkload:
+    name: str
+    fs: float
+    f_low: float
+    bank_spec: BankSpec  # parameter ranges of every bank (sizes differ)
+    banks: list  # [T_b, 4] float64 per bank, concatenated in this order for filtering
+    segments: list
+    blocks: list
+    k: int
+    w: int
+    rho_ii: float
+
+    @property
+    def bank(self) -> np.ndarray:
+        return np.concatenate(self.banks, axis=0)
+
+    def block_psd(self, b: BatchBlock) -> np.ndarray:
+        seg = self.segments[b.segment]
+        return analytic_psd(Grid(self.fs, b.n, self.f_low)) * seg.psd_scale
+
+    def block_strain(self, b: BatchBlock) -> np.ndarray:
+        return self.segments[b.segment].strain[b.offset:b.offset + b.n]
+
+    @property
+    def sizes(self) -> list:
+        return sorted({b.n for b in self.blocks})
+
+    @property
+    def valid_seconds(self) -> float:
+        return sum(b.n - b.valid_lo for b in self.blocks) / self.fs
+
+
+def segment_blocks(length: int, max_block: int) -> list:
+    """(offset, n, valid_lo) of the blocks of a segment of ``length`` samples: n is the largest
+    power of two <= min(length, max_block); blocks overlap by half; a last block is right-aligned
+    and keeps only the samples the block before it did not already cover."""
+    n = 1 << (min(length, max_block).bit_length() - 1)
+    out = []
+    off = 0
+    while off + n <= length:
+        out.append((off, n, n // 2))
+        off += n // 2
+    last_end = out[-1][0] + n
+    if last_end < length:
+        tail = length - n
+        out.append((tail, n, last_end - tail))
+    return out
+
+
+def batch(n_segments: int = 64, fs: float = 2048.0, f_low: float = 30.0, unit_s: float = 32.0,
+          max_units: int = 16, max_block_s: float = 128.0, n_banks: int = 4, bank_sizes=(5000, 20000),
+          m_range=(3.0, 50.0), chi_max: float = 0.5, pn_order: int = 3, k: int = 256, w: int = 8,
+          rho_ii: float = 5.0, inj_per_segment: int = 1, snr_range=(8.0, 15.0),
+          psd_scales=(0.5, 2.0), seed: int = 4) -> BatchWorkload:
+    """Segments of uneven length (uniform multiples of ``unit_s`` in [unit_s, max_units unit_s]) seen by
+    two detectors with independent noise and per-detector PSD scale factors, cut into blocks of
+    min(max_block_s, 2^floor(log2 L)) with half overlap; ``n_banks`` banks of sizes uniform in
+    ``bank_sizes`` drawn from the same parameter ranges (one basis serves all of them)."""
+    rng = np.random.default_rng(seed)
+    scales = rng.uniform(psd_scales[0], psd_scales[1], size=2)
+    sizes = rng.integers(bank_sizes[0], bank_sizes[1] + 1, size=n_banks)
+    spec = BankSpec(int(sizes.max()), m_range[0], m_range[1], chi_max, pn_order)
+    banks = [draw_bank(BankSpec(int(t), m_range[0], m_range[1], chi_max, pn_order), seed=SEED_BANK + 10 * b)
+             for b, t in enumerate(sizes)]
+    unit = int(round(unit_s * fs))
+    max_block = int(round(max_block_s * fs))
+    lengths = rng.integers(1, max_units + 1, size=n_segments) * unit
+    segments, blocks = [], []
+    start = 0
+    for s, length in enumerate(lengths):
+        for det in range(2):
+            grid = Grid(fs, int(length), f_low)
+            psd = analytic_psd(grid) * scales[det]
+            x = coloured_noise(grid, psd, noise_seed(s, det))
+            injs = draw_injections(spec, grid, inj_per_segment, snr_range, seed=SEED_INJ + 100 * s + det) \
+                if inj_per_segment else []
+            for inj in injs:
+                x = x + injection_series(grid, psd, inj, pn_order)
+            seg_index = len(segments)
+            segments.append(Segment(s, det, start, x.astype(np.float32), float(scales[det]), injs))
+            for off, n, lo in segment_blocks(int(length), max_block):
+                blocks.append(BatchBlock(seg_index, off, n, lo))
+        start += int(length)
+    name = f"batch-{n_segments}seg-x2det-{int(sum(sizes))}tmpl"
+    return BatchWorkload(name, fs, f_low, spec, banks, segments, blocks, k, w, rho_ii)

@@ -220,3 +220,29 @@ def test_overflow_and_errors(api):
     with pytest.raises(N.RBError) as e:
         api.rb_whiten(d, _dev(x), _dev(psd), ws=torch.empty(1024, dtype=torch.uint8, device="cuda"))
     assert e.value.code == N.RB_ERR_OOM
+
+
+@pytest.mark.parametrize("n,w", [(1 << 16, 8), (1 << 19, 2), (1 << 19, 16)])
+def test_fft_variants_identical(api, n, w):
+    """Every FFT schedule variant runs the same per-column arithmetic, so the basis series and
+    bin averages are bit-identical across variants; the tuner picks one of them."""
+    from paper_2110_13115_gb300 import _native as N
+
+    k = 20
+    g, psd, x = _strain(n, seed=4)
+    P = inputs.unit_rows(k, n // 2, seed=41).astype(np.complex64)
+    d = api.make_desc(g.fs, n, k, 4, w=w)
+    basis = api.Basis(_dev(P), _dev(_rand_coeff(4, k, 42).astype(np.complex64)), n)
+    ws = api.workspace(d)
+    sh = api.rb_whiten(d, _dev(x), _dev(psd), ws=ws)
+    outs = []
+    for v in range(N.RB_FFT_VARIANTS):
+        api.rb_set_fft_variant(d, v)
+        beta, bavg = api.rb_basis_filter(d, basis, sh, ws=ws)
+        outs.append((beta.cpu().numpy(), bavg.cpu().numpy()))
+    for beta, bavg in outs[1:]:
+        assert np.array_equal(beta, outs[0][0]) and np.array_equal(bavg, outs[0][1])
+    chosen, times = api.rb_tune_fft(d, basis, sh, ws=ws)
+    assert 0 <= chosen < N.RB_FFT_VARIANTS and all(t > 0 for t in times)
+    assert times[chosen] == min(times)
+    api.rb_set_fft_variant(d, 0)
