@@ -48,6 +48,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--rho-i", type=float, default=None, help="fixed first-stage threshold (skips calibration)")
+    p.add_argument("--workload", default="full", choices=["full", "batch"],
+                   help="full: one 256-s block (the headline); batch: uneven segments from two detectors, "
+                        "one CUDA-graph launch per step")
+    p.add_argument("--segments", type=int, default=64, help="segments of the batch workload")
+    p.add_argument("--fft-variant", type=int, default=None, help="pin the FFT schedule (skips its tuning)")
+    p.add_argument("--stage1-variant", type=int, default=None, help="pin the first-stage tile (skips its tuning)")
     return p.parse_args()
 
 
@@ -252,10 +258,123 @@ def accuracy(rb_trig, plain_trig, w, rho_ii):
                 missed_above_threshold=missed_clear)
 
 
+def run_batch(args):
+    """Batch workload: 64 segments of 32-512 s at 2048 Hz seen by two detectors (independent Gaussian
+    noise, PSD scale factors 0.5-2), blocks of min(128 s, 2^floor(log2 L)) with half overlap (FFT sizes
+    2^16-2^18), four banks of 5k-20k templates concatenated over one k = 256 basis per FFT size.
+    One step = one replay of the CUDA graph that filters every block (rb_batch_run)."""
+    import torch
+
+    from paper_2110_13115_gb300 import api, inputs, _native
+
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    _native.load()
+    # noise only, as in the paper's throughput runs (the batch tests inject signals)
+    wl = inputs.batch(n_segments=args.segments, k=args.k, w=args.w, seed=4 + rank, inj_per_segment=0)
+    bank = wl.bank
+    T = len(bank)
+    rho_i = 4.373 if args.rho_i is None else args.rho_i
+    t0 = time.perf_counter()
+    descs, bases, where = [], [], {}
+    for i, n in enumerate(wl.sizes):
+        psd1 = torch.from_numpy(inputs.analytic_psd(inputs.Grid(wl.fs, n, wl.f_low))).cuda()
+        b = api.rb_build(api.Bank(bank, wl.fs, n, wl.f_low, wl.bank_spec.pn_order), psd1, args.k, oversample=64,
+                         power_iters=1)
+        d = api.make_desc(wl.fs, n, args.k, T, w=args.w, precision=args.precision, rho_i=rho_i, rho_ii=wl.rho_ii,
+                          cand_capacity=1 << 25)
+        api.rb_pack_coeff(d, b)
+        descs.append(d)
+        bases.append(b)
+        where[n] = i
+        torch.cuda.empty_cache()
+    build_s = time.perf_counter() - t0
+
+    # every block's strain in one pinned host buffer and one device buffer; PSDs per (n, detector)
+    offs, tot = [], 0
+    for bb in wl.blocks:
+        offs.append(tot)
+        tot += bb.n
+    host = torch.empty(tot, dtype=torch.float32).pin_memory()
+    for bb, o in zip(wl.blocks, offs):
+        host[o:o + bb.n] = torch.from_numpy(np.ascontiguousarray(wl.block_strain(bb)))
+    dev = host.cuda()
+    psds = {}
+    blocks = []
+    for j, (bb, o) in enumerate(zip(wl.blocks, offs)):
+        seg = wl.segments[bb.segment]
+        key = (bb.n, seg.detector)
+        if key not in psds:
+            psds[key] = torch.from_numpy(wl.block_psd(bb)).cuda()
+        blocks.append(api.Block(strain=dev[o:o + bb.n], psd=psds[key], basis=where[bb.n],
+                                sample_offset=seg.start + bb.offset, valid_lo=bb.valid_lo, block_id=j))
+    ws = api.batch_workspace(descs)
+    tuned = {}
+    for n, i in where.items():  # tune each FFT size on its first block (setup, untimed)
+        blk = next(b for b in blocks if b.basis == i)
+        sh = api.rb_whiten(descs[i], blk.strain, blk.psd, ws=ws)
+        fv, ft = api.rb_tune_fft(descs[i], bases[i], sh, ws=ws)
+        entry = dict(fft_variant=fv, fft_ms=[round(t, 4) for t in ft])
+        if args.precision != "fp32":
+            _, bavg = api.rb_basis_filter(descs[i], bases[i], sh, keep_beta=False, ws=ws)
+            sv, st_ = api.rb_tune_stage1(descs[i], bases[i], bavg, ws=ws)
+            entry.update(stage1_variant=sv, stage1_ms=[round(t, 4) for t in st_])
+            del bavg
+        tuned[str(n)] = entry
+        del sh
+    cap = 1 << 25
+    batch = api.Batch(descs, bases, blocks, capacity=cap, ws=ws)
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = api.rb_kernel_launches()
+    with Clocks(local) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            _, nt = batch.run()
+        e1.record()
+        torch.cuda.synchronize()
+    launches = (api.rb_kernel_launches() - l0) // max(args.steps, 1)
+    ms = e0.elapsed_time(e1) / args.steps
+    tsec = T * wl.valid_seconds
+    value = tsec / (ms / 1e3)
+    # end to end: each step copies every block from pinned host memory, replays, reads the triggers
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.steps):
+        dev.copy_(host, non_blocking=True)
+        tb, n2 = batch.run()
+        out = tb[: n2 * 24].cpu()
+        d2h += out.numel()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t1) * 1e3 / args.steps
+    batch.close()
+    res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+               ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+               data="synthetic",
+               config=dict(workload=wl.name, segments=args.segments, detectors=2, blocks=len(wl.blocks),
+                           fft_sizes=wl.sizes, templates=T, banks=[len(b) for b in wl.banks],
+                           valid_seconds=wl.valid_seconds, k=args.k, w=args.w, rho_I=rho_i, rho_II=wl.rho_ii,
+                           first_stage=args.precision, graph="one CUDA graph replay per step", tuned=tuned,
+                           l2="inputs larger than L2: the bases alone are >= 134 MB each"),
+               e2e=dict(value=tsec / (e2e_ms / 1e3), unit=UNIT, h2d_bytes_per_step=tot * 4,
+                        d2h_bytes_per_step=d2h // max(args.steps, 1)),
+               gpu_launches=int(launches), clocks=clk.summary(), build_s=build_s, n_triggers=int(nt))
+    if rank == 0:
+        print(json.dumps(res))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -315,13 +434,21 @@ def main():
     api.rb_pack_coeff(d, basis)
     # autotune the FFT schedule and the first stage's tile variant on this block (setup, untimed)
     sh = api.rb_whiten(d, strain_d, psd_d, ws=ws)
-    fft_choice, fft_times = api.rb_tune_fft(d, basis, sh, ws=ws)
-    fft_tuned = dict(variant=fft_choice, ms_by_variant=[round(t, 4) for t in fft_times])
+    if args.fft_variant is None:
+        fft_choice, fft_times = api.rb_tune_fft(d, basis, sh, ws=ws)
+        fft_tuned = dict(variant=fft_choice, ms_by_variant=[round(t, 4) for t in fft_times])
+    else:
+        api.rb_set_fft_variant(d, args.fft_variant)
+        fft_tuned = dict(variant=args.fft_variant, pinned=True)
     if args.precision != "fp32":
-        _, bavg_t = api.rb_basis_filter(d, basis, sh, keep_beta=False, ws=ws)
-        chosen, times = api.rb_tune_stage1(d, basis, bavg_t, ws=ws)
-        tuned = dict(variant=chosen, n_tile=[256, 128][chosen], ms_by_variant=times)
-        del bavg_t
+        if args.stage1_variant is None:
+            _, bavg_t = api.rb_basis_filter(d, basis, sh, keep_beta=False, ws=ws)
+            chosen, times = api.rb_tune_stage1(d, basis, bavg_t, ws=ws)
+            tuned = dict(variant=chosen, n_tile=[256, 128][chosen], ms_by_variant=times)
+            del bavg_t
+        else:
+            api.rb_set_stage1_variant(d, args.stage1_variant)
+            tuned = dict(variant=args.stage1_variant, n_tile=[256, 128][args.stage1_variant], pinned=True)
     del sh
     cap = 1 << 23
     trig = torch.empty(cap * 24, dtype=torch.uint8, device="cuda")

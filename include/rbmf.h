@@ -328,7 +328,7 @@ int rb_tune_stage1(const rb_filter_desc* desc, const rb_basis* basis, const floa
  *   s_hat: [n/2] complex device (rb_whiten output). times_ms: HOST [RB_FFT_VARIANTS] mean ms of one
  *   basis filter. chosen: HOST, the selected variant. Synchronises `stream`.
  */
-#define RB_FFT_VARIANTS 6
+#define RB_FFT_VARIANTS 8
 int rb_tune_fft(const rb_filter_desc* desc, const rb_basis* basis, const float* s_hat, double* times_ms,
                 int32_t* chosen, void* workspace, size_t workspace_bytes, void* stream);
 /* rb_set_fft_variant - pin the FFT schedule variant used for desc's (n, w). Host only. */

@@ -21,7 +21,7 @@ RB_ERR_CUDA = -5
 RB_ERR_UNSUPPORTED = -6
 
 RB_STAGES = 6
-RB_FFT_VARIANTS = 6
+RB_FFT_VARIANTS = 8
 STAGE_NAMES = ["setup", "whiten", "basis_filter", "pack", "first_stage", "second_stage"]
 
 RB_PREC_FP32 = 0

@@ -145,7 +145,7 @@ void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws
   ws->wt = (float*)take(sizeof(float) * half);
   ws->shat = (float2*)take(sizeof(float2) * half);
   const int64_t nvec = plain ? d.n_templates : d.k;
-  int64_t vc = (int64_t(64) << 20) / (g.n * 8);  // four-step chunks of up to 64 MB (kept in L2)
+  int64_t vc = (int64_t(96) << 20) / (g.n * 8);  // four-step chunks of up to 96 MB (kept in L2)
   vc = std::max<int64_t>(1, std::min<int64_t>(vc, std::min<int64_t>(nvec, 65535)));
   ws->vc = (int)vc;
   ws->X = (float2*)take(sizeof(float2) * g.n * vc);

@@ -137,6 +137,28 @@ struct Radix {
   static_assert(r2 <= 16, "column length too long");
 };
 
+// Powers t[r] = w^r, r = 1..R-1, of one table twiddle w by binary powering (depth <= 4 products
+// for R = 16), so a butterfly reads one table entry instead of R - 1.
+template <int R>
+__device__ __forceinline__ void twiddle_powers(float2 w, float2 (&t)[R]) {
+  t[1] = w;
+  if constexpr (R > 2) {
+    t[2] = cmul(w, w);
+    t[3] = cmul(t[2], w);
+  }
+  if constexpr (R > 4) {
+    t[4] = cmul(t[2], t[2]);
+    t[5] = cmul(t[4], w);
+    t[6] = cmul(t[4], t[2]);
+    t[7] = cmul(t[4], t[3]);
+  }
+  if constexpr (R > 8) {
+    t[8] = cmul(t[4], t[4]);
+#pragma unroll
+    for (int r = 9; r < 16; ++r) t[r] = cmul(t[8], t[r - 8]);
+  }
+}
+
 // One Stockham pass of radix R after passes whose radices multiply to NS.
 // In:  v[b R + r] = x[j_b + r L/R];  Out: v[b R + r] = y[(j_b/NS) NS R + j_b % NS + r NS],
 // with j_b = tj + b (L/kE). tw[e] = exp(+2 pi i e / L).
@@ -147,12 +169,12 @@ __device__ __forceinline__ void radix_pass(float2 (&v)[kE], int tj, const float2
     if constexpr (NS > 1) {
       const int j = tj + b * (L / kE);
       const int jm = j & (NS - 1);
+      float2 w = tw[jm * (L / (NS * R))];  // exp(2 pi i jm / (NS R))
+      if (SIGN < 0) w.y = -w.y;
+      float2 t[R];
+      twiddle_powers<R>(w, t);
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 t = tw[(jm * r) * (L / (NS * R))];
-        if (SIGN < 0) t.y = -t.y;
-        v[b * R + r] = cmul(v[b * R + r], t);
-      }
+      for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], t[r]);
     }
     dft<R, SIGN>(&v[b * R]);
   }

@@ -500,7 +500,7 @@ struct FftVariant {
   int ga, gb, mb;
 };
 constexpr FftVariant kFftVariants[RB_FFT_VARIANTS] = {{8, 16, 32}, {4, 8, 32}, {4, 16, 32}, {8, 8, 32},
-                                                      {4, 8, 64}, {8, 16, 64}};
+                                                      {4, 8, 64}, {8, 16, 64}, {16, 16, 64}, {8, 16, 96}};
 
 int chunk_vectors(const rb::Geometry& g, const rb::Workspace& ws, const FftVariant& v) {
   const int64_t want = ((int64_t)v.mb << 20) / (g.n * 8);
