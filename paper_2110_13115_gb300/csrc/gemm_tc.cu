@@ -29,12 +29,14 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace {
 
+using namespace rbtma;
+
 constexpr int BM = 128, BK = 64;
 constexpr int kThreads = 320;  // producer warp, MMA warp, 8 epilogue warps
-constexpr uint64_t kWaitNs = 1000000000ull;
 
 struct TcParams {
   int T;          // templates (rows of A = 2T)
@@ -50,50 +52,6 @@ struct TcParams {
   unsigned* flags;
   uint32_t idesc;
 };
-
-__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(saddr(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Wait for the phase of parity `parity` to complete; false on abort or after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-  if (mbar_try(b, parity)) return true;
-  const uint64_t t0 = gtimer();
-  while (true) {
-    if (mbar_try(b, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtimer() - t0 > kWaitNs) return false;
-  }
-}
-
-__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar))
-      : "memory");
-}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -379,6 +337,38 @@ EncodeTiled encode_fn() {
   });
   return fn;
 }
+
+}  // namespace
+
+namespace rb {
+
+int make_map_2d(CUtensorMap* m, CUtensorMapDataType type, int elem_bytes, const void* base, uint64_t dim0,
+                uint64_t dim1, uint64_t row_bytes, uint32_t box0, uint32_t box1, CUtensorMapSwizzle swizzle) {
+  EncodeTiled enc = encode_fn();
+  if (!enc) {
+    set_detail("cuTensorMapEncodeTiled unavailable from the driver");
+    return RB_ERR_CUDA;
+  }
+  if (((uintptr_t)base & 15) || row_bytes % 16 || (box0 * elem_bytes) % 16) {
+    set_detail("tensor map base, row pitch or box width not 16-byte aligned");
+    return RB_ERR_BAD_INPUT;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)dim0, (cuuint64_t)dim1};
+  cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  cuuint32_t box[2] = {box0, box1};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, type, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_detail("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return RB_ERR_CUDA;
+  }
+  return RB_OK;
+}
+
+}  // namespace rb
+
+namespace {
 
 // 2D map over a [rows][kp] 16-bit matrix, box of 64 (K) x box_rows, 128-byte swizzle, zero fill.
 int make_map(CUtensorMap* m, const void* base, bool bf16, int64_t kp, int64_t rows, int box_rows) {

@@ -1,5 +1,6 @@
 // Internal host-side interfaces shared by the translation units of the library.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -55,6 +56,9 @@ struct Workspace {
 };
 
 void set_detail(const char* fmt, ...);
+// 2D TMA descriptor over [dim1][dim0] elements (row pitch row_bytes), box box0 x box1, zero fill.
+int make_map_2d(CUtensorMap* m, CUtensorMapDataType type, int elem_bytes, const void* base, uint64_t dim0,
+                uint64_t dim1, uint64_t row_bytes, uint32_t box0, uint32_t box1, CUtensorMapSwizzle swizzle);
 int make_geometry(const rb_filter_desc& d, Geometry* g);
 // base == nullptr: only compute the size (ws->total)
 void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws, bool plain);
