@@ -258,6 +258,38 @@ def accuracy(rb_trig, plain_trig, w, rho_ii):
                 missed_above_threshold=missed_clear)
 
 
+def cufft_comparator(torch, templates, s_hat, n, w, rho_ii, secs, sample=512, chunk=32, reps=3):
+    """The paper's comparator on the same GPU: per template, the elementwise product with the data
+    (whitened), a cuFFT inverse transform (torch.fft), |z|^2, the window maximum and the threshold.
+    Timed only, on a bounded sample of the bank; returns template-seconds/s."""
+    T = templates.shape[0]
+    sample = min(T, sample)
+    half = n // 2
+    q = torch.zeros((chunk, n), dtype=torch.complex64, device="cuda")
+    hits = torch.zeros((), dtype=torch.int64, device="cuda")
+
+    def run():
+        for t0 in range(0, sample, chunk):
+            c = min(chunk, sample - t0)
+            q[:c, :half] = s_hat[None, :] * templates[t0:t0 + c].conj()
+            z = torch.fft.ifft(q[:c], dim=1) * n
+            rho2 = (z[:, half:].abs() ** 2).reshape(c, -1, w)
+            hits.add_((rho2.amax(dim=2) >= rho_ii * rho_ii).sum())
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return dict(value=sample * secs / (ms / 1e3), unit=UNIT, ms_per_template=ms / sample,
+                impl="torch.fft (cuFFT) inverse FFT per template + elementwise product + threshold",
+                sample_templates=sample)
+
+
 def run_batch(args):
     """Batch workload: 64 segments of 32-512 s at 2048 Hz seen by two detectors (independent Gaussian
     noise, PSD scale factors 0.5-2), blocks of min(128 s, 2^floor(log2 L)) with half overlap (FFT sizes
@@ -265,14 +297,21 @@ def run_batch(args):
     One step = one replay of the CUDA graph that filters every block (rb_batch_run)."""
     import torch
 
-    from paper_2110_13115_gb300 import api, inputs, _native
+    from paper_2110_13115_gb300 import api, inputs, replicas, _native
 
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _native.load()
-    # noise only, as in the paper's throughput runs (the batch tests inject signals)
+    # noise only, as in the paper's throughput runs (the batch tests inject signals); every rank
+    # filters its own segments (independent replicas)
     wl = inputs.batch(n_segments=args.segments, k=args.k, w=args.w, seed=4 + rank, inj_per_segment=0)
     bank = wl.bank
     T = len(bank)
@@ -338,9 +377,8 @@ def run_batch(args):
         e1.record()
         torch.cuda.synchronize()
     launches = (api.rb_kernel_launches() - l0) // max(args.steps, 1)
-    ms = e0.elapsed_time(e1) / args.steps
     tsec = T * wl.valid_seconds
-    value = tsec / (ms / 1e3)
+    ms, value = replicas.job_rate(tsec, e0.elapsed_time(e1) / args.steps, dist, "cuda")
     # end to end: each step copies every block from pinned host memory, replays, reads the triggers
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -351,7 +389,7 @@ def run_batch(args):
         out = tb[: n2 * 24].cpu()
         d2h += out.numel()
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t1) * 1e3 / args.steps
+    e2e_ms, e2e_value = replicas.job_rate(tsec, (time.perf_counter() - t1) * 1e3 / args.steps, dist, "cuda")
     batch.close()
     res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
@@ -361,11 +399,13 @@ def run_batch(args):
                            valid_seconds=wl.valid_seconds, k=args.k, w=args.w, rho_I=rho_i, rho_II=wl.rho_ii,
                            first_stage=args.precision, graph="one CUDA graph replay per step", tuned=tuned,
                            l2="inputs larger than L2: the bases alone are >= 134 MB each"),
-               e2e=dict(value=tsec / (e2e_ms / 1e3), unit=UNIT, h2d_bytes_per_step=tot * 4,
+               e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=tot * 4,
                         d2h_bytes_per_step=d2h // max(args.steps, 1)),
                gpu_launches=int(launches), clocks=clk.summary(), build_s=build_s, n_triggers=int(nt))
     if rank == 0:
         print(json.dumps(res))
+    if dist:
+        dist.destroy_process_group()
 
 
 def main():
@@ -401,7 +441,7 @@ def main():
 
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2110_13115_gb300 import api, _native
+    from paper_2110_13115_gb300 import api, _native, replicas
 
     _native.load()
     g = wl.grid
@@ -471,14 +511,10 @@ def main():
         e1.record()
         torch.cuda.synchronize()
     launches = (api.rb_kernel_launches() - launches0) // max(args.steps, 1)
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
     secs_per_block = g.n // 2 / g.fs
-    value = world * T * secs_per_block / (ms / 1e3)
+    ms, value = replicas.job_rate(T * secs_per_block, e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    if dist:
+        dist.barrier()
     rb_trig = api.triggers_numpy(trig, nt)
 
     # per-stage timing (CUDA events recorded by the library on the launching stream)
@@ -501,12 +537,8 @@ def main():
         host_trig[: n_e * 24].copy_(trig[: n_e * 24], non_blocking=False)
         d2h_total += n_e * 24 + 24
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t_e2e) * 1e3 / args.steps
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * T * secs_per_block / (e2e_ms / 1e3)
+    e2e_ms, e2e_value = replicas.job_rate(T * secs_per_block, (time.perf_counter() - t_e2e) * 1e3 / args.steps,
+                                          dist, "cuda")
 
     # the template method on the same GPU (comparator) and the accuracy gate against it
     plain = None
@@ -529,6 +561,11 @@ def main():
                      impl="template method, fused Stockham FFT (this library)", speedup=pms / ms)
         acc = accuracy(rb_trig, api.triggers_numpy(ptrig, npl), args.w, wl.rho_ii)
         del wsp
+        sh_c = api.rb_whiten(d, strain_d, psd_d, ws=ws)
+        cufft = cufft_comparator(torch, templates, sh_c, g.n, args.w, wl.rho_ii, secs_per_block)
+        cufft["speedup"] = value / cufft["value"]
+        plain["cufft"] = cufft
+        del sh_c
 
     # roofline of the dominant stage
     peaks = {}
@@ -540,8 +577,21 @@ def main():
     tensor = peaks.get("bf16_tflops_sustained", 1700.0)
     smmax = peaks.get("sm_max_mhz", 2070.0)
     half, nb = g.n // 2, g.n // (2 * args.w)
-    dom = max(("basis_filter", "first_stage"), key=lambda s: stage_ms[s])
-    if dom == "first_stage":
+    dom = max(("basis_filter", "first_stage", "second_stage"), key=lambda s: stage_ms[s])
+    if dom == "second_stage":
+        # algorithmic work: k complex MACs for each of the w samples of every candidate (8 flop each)
+        sh_n = api.rb_whiten(d, strain_d, psd_d, ws=ws)
+        _, bavg_n = api.rb_basis_filter(d, basis, sh_n, keep_beta=False, ws=ws)
+        _, n_cand = api.rb_stage1(d, basis, bavg_n, ws=ws)
+        del sh_n, bavg_n
+        flops = 8.0 * args.k * args.w * n_cand
+        achieved = flops / (stage_ms[dom] / 1e3) / 1e12
+        roof = dict(bound="tensor", achieved=achieved, peak=tensor, unit="TFLOP/s", kernel="k_stage2_bins",
+                    peak_source="MEASURED_PEAKS bf16_tflops_sustained (the kernel issues mma.sync FP16, 3 products)",
+                    issued_mma_flops_ratio=3.0, candidates=int(n_cand),
+                    includes="bucketing kernels (count, scan, scatter) in the stage time")
+        key, srcs = roof["kernel"], ("paper_2110_13115_gb300/csrc/stage2.cu",)
+    elif dom == "first_stage":
         flops = 8.0 * T * args.k * nb
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
         if args.precision == "fp32":

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cmath>
 #include <map>
@@ -51,6 +52,7 @@ struct TcParams {
   long long cap;
   unsigned* flags;
   uint32_t idesc;
+  int withhold_copies;  // failure-detection test: the producer issues no copy (see rbx_stage1_withhold_copies)
 };
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -147,7 +149,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       int used = 0;  // stages that received at least one load
-      for (int tile = blockIdx.x; tile < num_tiles && !abort_flag; tile += gridDim.x) {
+      // (withhold_copies: no copy at all, so the MMA warp's first wait runs out and every role stops)
+      for (int tile = blockIdx.x; tile < num_tiles && !abort_flag && !p.withhold_copies; tile += gridDim.x) {
         int mb, nb;
         tile_coords(tile, p.num_m, p.num_n, mb, nb);
         for (int kb = 0; kb < p.KB; ++kb) {
@@ -429,6 +432,7 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
+std::atomic<int> g_withhold{0};  // launches left whose producer issues no copy (failure-detection test)
 std::map<TuneKey, int> g_tuned;
 
 int chosen_variant(const rb_filter_desc& d, const rb::Geometry& g) {
@@ -464,6 +468,7 @@ int build_params(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry&
   p.flags = ws.flags;
   const uint32_t fmt = bf ? 1u : 0u;
   p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  p.withhold_copies = 0;
   return RB_OK;
 }
 
@@ -479,6 +484,10 @@ int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, con
   TcParams p;
   int rc = build_params(d, b, g, ws, cand, v, maps, p);
   if (rc) return rc;
+  int left = g_withhold.load();
+  while (left > 0 && !g_withhold.compare_exchange_weak(left, left - 1)) {
+  }
+  p.withhold_copies = left > 0 ? 1 : 0;
   return launch_variant(v, split, maps, p, st);
 }
 
@@ -538,3 +547,11 @@ int set_stage1_variant(const rb_filter_desc& d, const Geometry& g, int variant) 
 }
 
 }  // namespace rb
+
+// Host-only test hook (not part of the C ABI): the next n tensor-core first-stage launches issue no
+// copies, so their bounded waits run out; the call reports RB_ERR_TIMEOUT and the context stays
+// usable. Used by the failure-detection test; no other code calls it.
+extern "C" int rbx_stage1_withhold_copies(int n) {
+  g_withhold.store(n > 0 ? n : 0);
+  return 0;
+}
