@@ -588,8 +588,7 @@ def main():
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
         roof = dict(bound="tensor", achieved=achieved, peak=tensor, unit="TFLOP/s", kernel="k_stage2_bins",
                     peak_source="MEASURED_PEAKS bf16_tflops_sustained (the kernel issues mma.sync FP16, 3 products)",
-                    issued_mma_flops_ratio=3.0, candidates=int(n_cand),
-                    includes="bucketing kernels (count, scan, scatter) in the stage time")
+                    issued_mma_flops_ratio=3.0, candidates=int(n_cand))
         key, srcs = roof["kernel"], ("paper_2110_13115_gb300/csrc/stage2.cu",)
     elif dom == "first_stage":
         flops = 8.0 * T * args.k * nb

@@ -341,8 +341,9 @@ enum {
   RB_STAGE_BASIS = 2,   /* a2 + a3 */
   RB_STAGE_PACK = 3,    /* first-stage operand packing (16-bit precisions) */
   RB_STAGE_FIRST = 4,   /* a4 contraction with fused threshold */
-  RB_STAGE_SECOND = 5,  /* a5 */
-  RB_STAGES = 6
+  RB_STAGE_BUCKET = 5,  /* a5 candidates bucketed by bin */
+  RB_STAGE_SECOND = 6,  /* a5 reconstruction of the candidates */
+  RB_STAGES = 7
 };
 
 /*

@@ -20,9 +20,9 @@ RB_ERR_TIMEOUT = -4
 RB_ERR_CUDA = -5
 RB_ERR_UNSUPPORTED = -6
 
-RB_STAGES = 6
+RB_STAGES = 7
 RB_FFT_VARIANTS = 8
-STAGE_NAMES = ["setup", "whiten", "basis_filter", "pack", "first_stage", "second_stage"]
+STAGE_NAMES = ["setup", "whiten", "basis_filter", "pack", "first_stage", "bucket", "second_stage"]
 
 RB_PREC_FP32 = 0
 RB_PREC_FP16_SPLIT = 1

@@ -637,8 +637,10 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
     return rc;
   mk.to(RB_STAGE_PACK);
   if ((rc = run_stage1(*desc, *basis, g, ws, ws.bavg, ws.cand, st, &mk))) return rc;
+  mk.to(RB_STAGE_BUCKET);
+  if ((rc = stage2_bucket(*desc, g, ws, 0, st))) return rc;
   mk.to(RB_STAGE_SECOND);
-  if ((rc = stage2_bucketed(*desc, *basis, g, ws, ws.beta, trig, capacity, ws.trig_count, 0, st))) return rc;
+  if ((rc = stage2_run(*desc, *basis, g, ws, ws.beta, trig, capacity, ws.trig_count, st))) return rc;
   mk.finish();
   Status s;
   if ((rc = read_status(ws, &s, st))) return rc;

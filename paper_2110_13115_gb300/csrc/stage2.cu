@@ -351,9 +351,7 @@ int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& 
 
 namespace rb {
 
-int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-                    const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, int bin_lo,
-                    cudaStream_t st) {
+int stage2_bucket(const rb_filter_desc& d, const Geometry& g, const Workspace& ws, int bin_lo, cudaStream_t st) {
   const int nb = (int)g.n_bins;
   const int bin0 = nb;  // valid bins are [n/(2w), n/w)
   RB_CUDA_TRY(cudaMemsetAsync(ws.bin_count, 0, sizeof(unsigned) * (nb + 1), st));
@@ -365,6 +363,11 @@ int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& 
   k_bin_scatter<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, ws.bin_start,
                                          ws.bin_count, ws.cand_sorted);
   RB_LAUNCH_CHECK();
+  return RB_OK;
+}
+
+int stage2_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
+               const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st) {
   switch (d.w) {
     case 1: return launch_bins<1>(d, b, g, ws, beta, trig, cap, counter, st);
     case 2: return launch_bins<2>(d, b, g, ws, beta, trig, cap, counter, st);
@@ -373,6 +376,14 @@ int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& 
     case 16: return launch_bins<16>(d, b, g, ws, beta, trig, cap, counter, st);
   }
   return RB_ERR_BAD_INPUT;
+}
+
+int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
+                    const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, int bin_lo,
+                    cudaStream_t st) {
+  int rc = stage2_bucket(d, g, ws, bin_lo, st);
+  if (rc) return rc;
+  return stage2_run(d, b, g, ws, beta, trig, cap, counter, st);
 }
 
 }  // namespace rb
