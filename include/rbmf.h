@@ -50,7 +50,8 @@ enum {
   RB_PREC_FP16_SPLIT = 1,  /* tcgen05 FP16 operands split hi+lo, 3 MMAs, FP32 accumulate */
   RB_PREC_BF16_SPLIT = 2,  /* tcgen05 BF16 operands split hi+lo, 3 MMAs, FP32 accumulate */
   RB_PREC_FP16 = 3,        /* tcgen05 single FP16 operands, FP32 accumulate */
-  RB_PREC_BF16 = 4         /* tcgen05 single BF16 operands, FP32 accumulate */
+  RB_PREC_BF16 = 4,        /* tcgen05 single BF16 operands, FP32 accumulate */
+  RB_PREC_FP16_SPLIT_A = 5 /* tcgen05 FP16, coefficients split hi+lo, beta_avg single: 2 MMAs */
 };
 
 /* One block's filtering parameters. */

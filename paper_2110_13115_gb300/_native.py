@@ -29,7 +29,8 @@ RB_PREC_FP16_SPLIT = 1
 RB_PREC_BF16_SPLIT = 2
 RB_PREC_FP16 = 3
 RB_PREC_BF16 = 4
-PRECISIONS = {"fp32": 0, "fp16_split": 1, "bf16_split": 2, "fp16": 3, "bf16": 4}
+RB_PREC_FP16_SPLIT_A = 5
+PRECISIONS = {"fp32": 0, "fp16_split": 1, "bf16_split": 2, "fp16": 3, "bf16": 4, "fp16_split_a": 5}
 
 
 class rb_filter_desc(C.Structure):

@@ -102,7 +102,7 @@ int make_geometry(const rb_filter_desc& d, Geometry* g) {
     set_detail("cand_capacity must be in [0, 2^31) and reserved must be 0");
     return RB_ERR_BAD_INPUT;
   }
-  if (d.precision < RB_PREC_FP32 || d.precision > RB_PREC_BF16) {
+  if (d.precision < RB_PREC_FP32 || d.precision > RB_PREC_FP16_SPLIT_A) {
     set_detail("unknown precision %d", d.precision);
     return RB_ERR_UNSUPPORTED;
   }
@@ -118,8 +118,10 @@ int make_geometry(const rb_filter_desc& d, Geometry* g) {
 }
 
 size_t coeff_op_bytes(const rb_filter_desc& d, const Geometry& g) {
-  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
-  const size_t stage1 = d.precision == RB_PREC_FP32 ? 0 : (split ? 2 : 1) * (size_t)2 * d.n_templates * g.kp * 2;
+  // A planes of the first stage: hi and lo for the split precisions (B split or not), else one
+  const bool split_a = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT ||
+                       d.precision == RB_PREC_FP16_SPLIT_A;
+  const size_t stage1 = d.precision == RB_PREC_FP32 ? 0 : (split_a ? 2 : 1) * (size_t)2 * d.n_templates * g.kp * 2;
   return g.s2_bytes + stage1;
 }
 

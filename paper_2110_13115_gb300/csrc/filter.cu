@@ -670,7 +670,9 @@ int pack_coeff(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, vo
   if (d.precision == RB_PREC_FP32) return RB_OK;
   void* out = (char*)out_all + g.s2_bytes;
   const int64_t plane = (int64_t)2 * d.n_templates * g.kp;
-  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
+  // A in hi and lo planes for every split precision (the B operand is split only for the first two)
+  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT ||
+                     d.precision == RB_PREC_FP16_SPLIT_A;
   const bool bf = d.precision == RB_PREC_BF16 || d.precision == RB_PREC_BF16_SPLIT;
   const int blocks = (int)std::min<int64_t>(4096, (plane + 255) / 256);
   if (bf) {

@@ -100,12 +100,14 @@ __device__ __forceinline__ void tile_coords(int tile, int num_m, int num_n, int&
   nb = tile / num_m;
 }
 
-template <int NPLANES, int STAGES, int BN>
+// NA / NB: planes of A / B (1: one 16-bit operand; 2: hi and lo). Products per K step:
+// (1, 1) a.b; (2, 2) hi.hi + hi.lo + lo.hi; (2, 1) hi.b + lo.b (A exact to about 22 bits, B rounded).
+template <int NA, int NB, int STAGES, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_stage1_tc(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                 const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1, TcParams p) {
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-  constexpr uint32_t STAGE_BYTES = NPLANES * (A_BYTES + B_BYTES);
+  constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_slot;
@@ -161,9 +163,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t sb = smem0 + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], STAGE_BYTES);
           tma_load(sb, &tmA0, &full[stage], kb * BK, mb * BM);
-          if (NPLANES == 2) tma_load(sb + A_BYTES, &tmA1, &full[stage], kb * BK, mb * BM);
-          tma_load(sb + NPLANES * A_BYTES, &tmB0, &full[stage], kb * BK, nb * BN);
-          if (NPLANES == 2) tma_load(sb + NPLANES * A_BYTES + B_BYTES, &tmB1, &full[stage], kb * BK, nb * BN);
+          if (NA == 2) tma_load(sb + A_BYTES, &tmA1, &full[stage], kb * BK, mb * BM);
+          tma_load(sb + NA * A_BYTES, &tmB0, &full[stage], kb * BK, nb * BN);
+          if (NB == 2) tma_load(sb + NA * A_BYTES + B_BYTES, &tmB1, &full[stage], kb * BK, nb * BN);
           used = used < STAGES ? used + 1 : STAGES;
           if (++stage == STAGES) {
             stage = 0;
@@ -206,16 +208,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t a0 = smem0 + stage * STAGE_BYTES;
           const uint32_t a1 = a0 + A_BYTES;
-          const uint32_t b0 = a0 + NPLANES * A_BYTES;
+          const uint32_t b0 = a0 + NA * A_BYTES;
           const uint32_t b1 = b0 + B_BYTES;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint32_t off = kk * 32;
             tc_mma(d, sw128_desc(a0 + off), sw128_desc(b0 + off), p.idesc, (kb | kk) != 0);
-            if (NPLANES == 2) {
-              tc_mma(d, sw128_desc(a0 + off), sw128_desc(b1 + off), p.idesc, 1);
-              tc_mma(d, sw128_desc(a1 + off), sw128_desc(b0 + off), p.idesc, 1);
-            }
+            if (NB == 2) tc_mma(d, sw128_desc(a0 + off), sw128_desc(b1 + off), p.idesc, 1);
+            if (NA == 2) tc_mma(d, sw128_desc(a1 + off), sw128_desc(b0 + off), p.idesc, 1);
           }
           issued = true;
           tc_commit(&empty[stage]);
@@ -398,11 +398,11 @@ int make_map(CUtensorMap* m, const void* base, bool bf16, int64_t kp, int64_t ro
   return RB_OK;
 }
 
-template <int NPLANES, int STAGES, int BN>
+template <int NA, int NB, int STAGES, int BN>
 int launch_tc(const CUtensorMap* maps, const TcParams& p, cudaStream_t st) {
-  constexpr int smem = STAGES * NPLANES * (BM * BK * 2 + BN * BK * 2) + 1024;
+  constexpr int smem = STAGES * (NA * BM * BK * 2 + NB * BN * BK * 2) + 1024;
   static_assert(smem <= 227 * 1024, "shared memory budget");
-  auto kern = k_stage1_tc<NPLANES, STAGES, BN>;
+  auto kern = k_stage1_tc<NA, NB, STAGES, BN>;
   RB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int dev = 0, sms = 0;
   RB_CUDA_TRY(cudaGetDevice(&dev));
@@ -418,9 +418,22 @@ int launch_tc(const CUtensorMap* maps, const TcParams& p, cudaStream_t st) {
 constexpr int kVariants = 2;
 constexpr int kVariantBN[kVariants] = {256, 128};
 
-int launch_variant(int v, bool split, const CUtensorMap* maps, const TcParams& p, cudaStream_t st) {
-  if (v == 0) return split ? launch_tc<2, 2, 256>(maps, p, st) : launch_tc<1, 4, 256>(maps, p, st);
-  return split ? launch_tc<2, 3, 128>(maps, p, st) : launch_tc<1, 6, 128>(maps, p, st);
+// planes: 1 (single operands), 2 (A and B split), 3 (A split, B single)
+int launch_variant(int v, int planes, const CUtensorMap* maps, const TcParams& p, cudaStream_t st) {
+  if (v == 0) {
+    if (planes == 2) return launch_tc<2, 2, 2, 256>(maps, p, st);
+    if (planes == 3) return launch_tc<2, 1, 3, 256>(maps, p, st);
+    return launch_tc<1, 1, 4, 256>(maps, p, st);
+  }
+  if (planes == 2) return launch_tc<2, 2, 3, 128>(maps, p, st);
+  if (planes == 3) return launch_tc<2, 1, 4, 128>(maps, p, st);
+  return launch_tc<1, 1, 6, 128>(maps, p, st);
+}
+
+int plane_mode(int precision) {
+  if (precision == RB_PREC_FP16_SPLIT || precision == RB_PREC_BF16_SPLIT) return 2;
+  if (precision == RB_PREC_FP16_SPLIT_A) return 3;
+  return 1;
 }
 
 struct TuneKey {
@@ -444,11 +457,13 @@ int chosen_variant(const rb_filter_desc& d, const rb::Geometry& g) {
 int build_params(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
                  rb_candidate* cand, int variant, CUtensorMap* maps, TcParams& p) {
   const int BN = kVariantBN[variant];
-  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
+  const int planes = plane_mode(d.precision);
+  const bool split = planes == 2;                  // B in hi and lo planes
+  const bool split_a = planes == 2 || planes == 3;  // A in hi and lo planes
   const bool bf = d.precision == RB_PREC_BF16 || d.precision == RB_PREC_BF16_SPLIT;
   const int64_t M = 2 * (int64_t)d.n_templates;
   const uint16_t* a0 = (const uint16_t*)((const char*)b.coeff_op + g.s2_bytes);
-  const uint16_t* a1 = split ? a0 + M * g.kp : a0;
+  const uint16_t* a1 = split_a ? a0 + M * g.kp : a0;
   int rc;
   if ((rc = make_map(&maps[0], a0, bf, g.kp, M, BM))) return rc;
   if ((rc = make_map(&maps[1], a1, bf, g.kp, M, BM))) return rc;
@@ -478,7 +493,7 @@ namespace rb {
 
 int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws, rb_candidate* cand,
               cudaStream_t st) {
-  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
+  const int planes = plane_mode(d.precision);
   const int v = chosen_variant(d, g);
   CUtensorMap maps[4];
   TcParams p;
@@ -488,14 +503,14 @@ int stage1_tc(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, con
   while (left > 0 && !g_withhold.compare_exchange_weak(left, left - 1)) {
   }
   p.withhold_copies = left > 0 ? 1 : 0;
-  return launch_variant(v, split, maps, p, st);
+  return launch_variant(v, planes, maps, p, st);
 }
 
 // Time every variant on the packed operands in the workspace (threshold disabled so no candidate is
 // written), remember the fastest for this shape and precision, and report the times.
 int tune_stage1(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws, double* ms,
                 int* chosen, cudaStream_t st) {
-  const bool split = d.precision == RB_PREC_FP16_SPLIT || d.precision == RB_PREC_BF16_SPLIT;
+  const int planes = plane_mode(d.precision);
   cudaEvent_t e0, e1;
   RB_CUDA_TRY(cudaEventCreate(&e0));
   RB_CUDA_TRY(cudaEventCreate(&e1));
@@ -506,10 +521,10 @@ int tune_stage1(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, c
     TcParams p;
     if ((rc = build_params(d, b, g, ws, ws.cand, v, maps, p))) break;
     p.thr2 = INFINITY;
-    if ((rc = launch_variant(v, split, maps, p, st))) break;  // warm-up
+    if ((rc = launch_variant(v, planes, maps, p, st))) break;  // warm-up
     const int reps = 3;
     if (cudaEventRecord(e0, st) != cudaSuccess) rc = RB_ERR_CUDA;
-    for (int r = 0; r < reps && rc == RB_OK; ++r) rc = launch_variant(v, split, maps, p, st);
+    for (int r = 0; r < reps && rc == RB_OK; ++r) rc = launch_variant(v, planes, maps, p, st);
     if (rc) break;
     float t = 0.f;
     if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

@@ -1,7 +1,8 @@
 """Precision pattern of the first stage (Sec. III.C first stage as a contraction over the basis,
 Eq. 7 applied to the bin averages of Eq. 9): the same reduced-basis pipeline run with the
 reconstruction GEMM in FP32 (SIMT), FP16 and BF16 split hi + lo (three tensor-core products,
-FP32 accumulate) and plain FP16 and BF16, on the 50,000-template / k = 400 precision workload.
+FP32 accumulate), FP16 with only the coefficients split (two products), and plain FP16 and BF16, on
+the 50,000-template / k = 400 precision workload.
 
 For every precision the first-stage candidates' |z_avg| and the triggers' |z| are compared with
 FP64 values computed by the oracle from the same basis and coefficients:
@@ -23,10 +24,10 @@ from paper_2110_13115_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-PRECISIONS = ["fp32", "fp16_split", "bf16_split", "fp16", "bf16"]
+PRECISIONS = ["fp32", "fp16_split", "bf16_split", "fp16_split_a", "fp16", "bf16"]
 # the benchmark spec's tolerance on the FP32 SNR holds for the FP32 and split paths; the plain 16-bit
 # paths are reported (about 2^-9 and 2^-12 relative per operand), with a loose sanity bound
-BOUND = {"fp32": 1e-5, "fp16_split": 1e-4, "bf16_split": 1e-4, "fp16": 2e-2, "bf16": 5e-2}
+BOUND = {"fp32": 1e-5, "fp16_split": 1e-4, "bf16_split": 1e-4, "fp16_split_a": 2e-3, "fp16": 2e-2, "bf16": 5e-2}
 SAMPLE = 200_000  # candidates compared per precision (all of them when fewer; top SNRs always)
 
 

@@ -11,8 +11,9 @@ from parity_util import compare_triggers
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# worst relative error of |z_avg| expected per precision (hi+lo splits keep ~16-22 bits)
-REL = {"fp16_split": 2e-5, "bf16_split": 1e-4, "fp16": 3e-3, "bf16": 2e-2}
+# worst relative error of |z_avg| expected per precision (hi+lo splits keep ~16-22 bits; splitting only
+# the coefficients leaves beta_avg's FP16 rounding, about 2^-11 per element)
+REL = {"fp16_split": 2e-5, "bf16_split": 1e-4, "fp16": 3e-3, "bf16": 2e-2, "fp16_split_a": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +44,7 @@ def _case(api, T, k, n, w, rho_i, prec, seed=1, variant=0):
 
 
 @pytest.mark.parametrize("variant", [0, 1])
-@pytest.mark.parametrize("prec", ["fp16_split", "bf16_split", "fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp16_split", "bf16_split", "fp16", "bf16", "fp16_split_a"])
 @pytest.mark.parametrize("T,k,n,w", [(64, 32, 1 << 14, 16),  # one M tile, two N tiles, K = 64
                                      (200, 24, 1 << 14, 8),  # ragged M (400 rows), ragged K (48 -> 64)
                                      (333, 96, 1 << 15, 4),  # ragged M, N = 4096, K = 192
@@ -88,7 +89,8 @@ def test_stage1_tc_overflow_reports_count(api):
     assert e.value.code == N.RB_ERR_OVERFLOW
 
 
-@pytest.mark.parametrize("prec,w,rho_i", [("fp16_split", 8, 2.5), ("fp16", 4, 3.0), ("bf16_split", 16, 2.0)])
+@pytest.mark.parametrize("prec,w,rho_i", [("fp16_split", 8, 2.5), ("fp16", 4, 3.0), ("bf16_split", 16, 2.0),
+                                          ("fp16_split_a", 8, 2.5)])
 def test_pipeline_tc_real_bank_vs_oracle_rb(api, prec, w, rho_i):
     """GPU rb_build + rb_filter (tensor-core first stage) against the oracle's SVD + hierarchy."""
     k = 40
