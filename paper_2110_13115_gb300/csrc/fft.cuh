@@ -121,6 +121,39 @@ __device__ __forceinline__ void dft16v(float2* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = t[i];
 }
+// dft16v for inputs whose upper half v[8..15] is zero (a one-sided spectrum's first pass): the first
+// radix-4 stage reduces to (a0 + a1, a0 + SIGN i a1, a0 - a1, a0 - SIGN i a1).
+template <int SIGN>
+__device__ __forceinline__ void dft16_half(float2* v) {
+#pragma unroll
+  for (int r2 = 0; r2 < 4; ++r2) {
+    const float2 a0 = v[r2], a1 = v[r2 + 4];
+    const float2 ia1 = mul_i<SIGN>(a1);
+    v[r2] = cadd(a0, a1);
+    v[r2 + 4] = cadd(a0, ia1);
+    v[r2 + 8] = csub(a0, a1);
+    v[r2 + 12] = csub(a0, ia1);
+  }
+  v[5] = cmul(v[5], w16<SIGN, 1>());
+  v[6] = cmul(v[6], w16<SIGN, 2>());
+  v[7] = cmul(v[7], w16<SIGN, 3>());
+  v[9] = cmul(v[9], w16<SIGN, 2>());
+  v[10] = mul_i<SIGN>(v[10]);
+  v[11] = cmul(v[11], w16<SIGN, 6>());
+  v[13] = cmul(v[13], w16<SIGN, 3>());
+  v[14] = cmul(v[14], w16<SIGN, 6>());
+  v[15] = cmul(v[15], w16<SIGN, 9>());
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  float2 t[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
 template <>
 __device__ __forceinline__ void dft<16, 1>(float2* v) { dft16v<1>(v); }
 template <>
@@ -202,16 +235,25 @@ struct Smem {
 
 // The whole column transform: pass 0 reads through `load(point)`, the last pass leaves
 // v[b Rl + r] holding output point out_pos<L, Rl, NSl>(tj, b, r). Returns via v.
-template <int SIGN, int L, int G, class Load>
+// HALF: the input points >= L/2 are zero (a one-sided spectrum); with a first pass of radix 16 that
+// holds all of a thread's points (R0 = kE), they are exactly the thread's r >= 8 and are neither
+// loaded nor added.
+template <int SIGN, int L, int G, bool HALF = false, class Load>
 __device__ __forceinline__ void column_transform(float2 (&v)[kE], int c, int tj, float2* sdata,
                                                  const float2* tw, Load load) {
   using P = Radix<L>;
   constexpr int R0 = P::r0, R1 = P::r1, R2 = P::r2;
+  if constexpr (HALF && R0 == kE && R0 == 16) {
 #pragma unroll
-  for (int b = 0; b < kE / R0; ++b)
+    for (int r = 0; r < R0; ++r) v[r] = r < R0 / 2 ? load(in_pos<L, R0>(tj, 0, r)) : make_float2(0.f, 0.f);
+    dft16_half<SIGN>(v);
+  } else {
 #pragma unroll
-    for (int r = 0; r < R0; ++r) v[b * R0 + r] = load(in_pos<L, R0>(tj, b, r));
-  radix_pass<SIGN, L, R0, 1>(v, tj, tw);
+    for (int b = 0; b < kE / R0; ++b)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) v[b * R0 + r] = load(in_pos<L, R0>(tj, b, r));
+    radix_pass<SIGN, L, R0, 1>(v, tj, tw);
+  }
   if constexpr (R1 > 1) {
     __syncthreads();
 #pragma unroll

@@ -97,19 +97,28 @@ __global__ void __launch_bounds__(G * L / kE) k_pass_a(const float2* __restrict_
       return cmulc(__ldg(shat + j), __ldcs(row + j));
     }
   };
-  column_transform<SIGN, L, G>(v, c, tj, sdata, tw, load);
+  column_transform<SIGN, L, G, MODE == MODE_BANK>(v, c, tj, sdata, tw, load);
   __syncthreads();
-  constexpr int RL = LastPass<L>::R;
+  // twiddle w_n^(j1 m2): the last pass's outputs are m2 = m2_0(b) + r NS, so each butterfly takes one
+  // table value w_n^(j1 m2_0) and the powers of w_n^(j1 NS), shared by the thread's butterflies
+  constexpr int RL = LastPass<L>::R, NSL = LastPass<L>::NS;
+  auto tw_n = [&](int rr) {  // w_n^rr, rr < n, from the two-level table
+    float2 t = cmul(__ldg(tab_n1 + (rr >> LOG2L)), __ldg(tab_fine + (rr & (L - 1))));
+    if (SIGN < 0) t.y = -t.y;
+    return t;
+  };
+  float2 sp[RL];
+  if constexpr (RL > 1) twiddle_powers<RL>(tw_n(j1 * NSL), sp);
 #pragma unroll
-  for (int b = 0; b < kE / RL; ++b)
+  for (int b = 0; b < kE / RL; ++b) {
+    const int m20 = final_point<L>(tj, b, 0);
+    const float2 base = tw_n(j1 * m20);  // j1 m2 < n
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
-      const int m2 = final_point<L>(tj, b, r);
-      const int rr = j1 * m2;  // < n
-      float2 t = cmul(__ldg(tab_n1 + (rr >> LOG2L)), __ldg(tab_fine + (rr & (L - 1))));
-      if (SIGN < 0) t.y = -t.y;
-      sdata[c * (L + 1) + m2] = cmul(v[b * RL + r], t);
+      const float2 t = r == 0 ? base : cmul(base, sp[r]);
+      sdata[c * (L + 1) + m20 + r * NSL] = cmul(v[b * RL + r], t);
     }
+  }
   __syncthreads();
   float2* xo = X + ((int64_t)blockIdx.y * n1 + (int64_t)blockIdx.x * G) * L;
   for (int idx = tid; idx < G * L; idx += blockDim.x) {
@@ -166,7 +175,10 @@ __global__ void __launch_bounds__(G * L / kE) k_pass_b(PassBArgs a, const float2
   column_transform<SIGN, L, G>(v, c, tj, sdata, tw, load);
   const int64_t n = (int64_t)L * n2, half = n / 2;
   const int64_t vec = a.vec0 + blockIdx.y;
+  // the last pass's outputs are m1 = j + r NS with j < NS = L / RL, so m1 >= L/2 exactly when
+  // r >= RL/2: the half that is not kept is known at compile time and never finished or stored
   constexpr int RL = LastPass<L>::R;
+  static_assert(RL >= 2 && LastPass<L>::NS * RL == L, "last pass layout");
 #pragma unroll
   for (int b = 0; b < kE / RL; ++b)
 #pragma unroll
@@ -175,20 +187,19 @@ __global__ void __launch_bounds__(G * L / kE) k_pass_b(PassBArgs a, const float2
       const int64_t m = m2 + (int64_t)n2 * m1;
       const float2 val = v[b * RL + r];
       if constexpr (MODE == MODE_STRAIN) {
-        if (m1 < L / 2) a.shat[m] = cscale(val, __ldg(a.wt + m));
+        if (r < RL / 2) a.shat[m] = cscale(val, __ldg(a.wt + m));
       } else if constexpr (MODE == MODE_BANK) {
+        if (r < RL / 2) continue;
         float2 s = val;
 #pragma unroll
         for (int off = 1; off < W; off <<= 1) {
           s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
           s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
         }
-        if (m1 >= L / 2) {
-          if (a.beta) __stcs(a.beta + vec * half + (m - half), val);
-          if ((c & (W - 1)) == 0)
-            a.beta_avg[vec * (half / W) + (m - half) / W] = cscale(s, 1.0f / W);
-        }
+        if (a.beta) __stcs(a.beta + vec * half + (m - half), val);
+        if ((c & (W - 1)) == 0) a.beta_avg[vec * (half / W) + (m - half) / W] = cscale(s, 1.0f / W);
       } else {
+        if (r < RL / 2) continue;
         float r2 = cabs2(val);
         int64_t mb = m;
         float2 vb = val;
@@ -204,7 +215,7 @@ __global__ void __launch_bounds__(G * L / kE) k_pass_b(PassBArgs a, const float2
             vb = make_float2(vx, vy);
           }
         }
-        if (m1 >= L / 2 && (c & (W - 1)) == 0 && r2 >= a.thr2) {
+        if ((c & (W - 1)) == 0 && r2 >= a.thr2) {
           const unsigned long long idx = atomicAdd(a.counter, 1ull);
           if ((int64_t)idx < a.cap) {
             rb_trigger t;
