@@ -52,25 +52,26 @@ __global__ void k_bin_count(const rb_candidate* __restrict__ cand, const unsigne
 // pieces {bin, first, end} of at most kPiece consecutive bucketed candidates, so that the
 // second stage can spread a bin with thousands of candidates over many CTAs and skips empty
 // bins entirely. Counts and piece counts are scanned together as one 64-bit value (pieces in the
-// high word). One CTA of 1024 threads walks the array in tiles of 8192 counters, each thread
-// scanning 8 consecutive ones, with a running carry between tiles.
+// high word). One CTA of 1024 threads walks the array in tiles of 16384 counters, each thread
+// scanning 16 consecutive ones, with a running carry between tiles.
 __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count, unsigned* __restrict__ start, int nb,
                                                    int4* __restrict__ pieces, unsigned* __restrict__ piece_total) {
   using u64 = unsigned long long;
+  constexpr int PER = 16;  // counters per thread: one tile covers 16384 bins
   __shared__ u64 wsum[32];
   __shared__ u64 carry_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto packed = [](unsigned c) { return (u64)c | ((u64)((c + kPiece - 1) / kPiece) << 32); };
   if (tid == 0) carry_s = 0;
   __syncthreads();
-  for (int base = 0; base < nb; base += 8192) {
-    u64 v[8];
+  for (int base = 0; base < nb; base += 1024 * PER) {
+    unsigned v[PER];
     u64 s = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int i = base + tid * 8 + j;
-      const unsigned c = i < nb ? count[i] : 0u;
-      v[j] = (u64)c | ((u64)((c + kPiece - 1) / kPiece) << 32);
-      s += v[j];
+    for (int j = 0; j < PER; ++j) {
+      const int i = base + tid * PER + j;
+      v[j] = i < nb ? count[i] : 0u;
+      s += packed(v[j]);
     }
     u64 inc = s;
 #pragma unroll
@@ -93,16 +94,16 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
     __syncthreads();
     u64 run = carry_s + wsum[warp] + inc - s;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int i = base + tid * 8 + j;
+    for (int j = 0; j < PER; ++j) {
+      const int i = base + tid * PER + j;
       if (i < nb) {
-        const unsigned c0 = (unsigned)run, c = (unsigned)v[j], p0 = (unsigned)(run >> 32);
+        const unsigned c0 = (unsigned)run, c = v[j], p0 = (unsigned)(run >> 32);
         start[i] = c0;
         count[i] = 0;
         for (unsigned q = 0; q * kPiece < c; ++q)
           pieces[p0 + q] = make_int4(i, (int)(c0 + q * kPiece), (int)(c0 + min(c, (q + 1) * kPiece)), 0);
       }
-      run += v[j];
+      run += packed(v[j]);
     }
     __syncthreads();
     if (tid == 1023) carry_s = run;
