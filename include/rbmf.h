@@ -171,7 +171,8 @@ int rb_pack_coeff(const rb_filter_desc* desc, const rb_basis* basis, void* out, 
  * (Eq. 7 applied to Eq. 9) as one contraction over K = 2k, with |z_avg| >= rho_I tested in the
  * epilogue so the T x bins array never reaches memory (Sec. III.C first stage; Sec. III.E).
  * RB_PREC_FP32 runs an FP32 SIMT kernel; the 16-bit precisions run a tcgen05 kernel whose
- * operands TMA loads into shared memory and whose accumulators live in tensor memory.
+ * operands TMA loads into shared memory and whose accumulators live in tensor memory (one, two
+ * or three products per K step by precision; every device wait is bounded, RB_ERR_TIMEOUT).
  *   beta_avg: [k][n/(2w)] complex (rb_basis_filter output).
  *   cand: [desc->cand_capacity] output; n_cand (host): number found. Synchronises `stream`.
  *   Errors: RB_ERR_OVERFLOW when more than cand_capacity candidates exist (*n_cand = count,
@@ -183,12 +184,17 @@ int rb_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* be
               void* stream);
 
 /*
- * rb_stage2 - step a5: for each candidate (t, i), z_t[m] = sum_k conj(a_tk) beta_k[m] in FP32
- * for m in [i w, i w + w); emit the arg-max (ties to the smaller m) when |z| >= rho_II
- * (Sec. III.C second stage, Sec. III.E custom kernel). One warp per candidate, lanes split k.
+ * rb_stage2 - step a5: for each candidate (t, i), z_t[m] = sum_k conj(a_tk) beta_k[m] to FP32
+ * accuracy for m in [i w, i w + w); emit the arg-max (ties to the smaller m) when |z| >= rho_II
+ * (Sec. III.C second stage, Sec. III.E custom kernel). Candidates are bucketed by bin (any
+ * input order); for each bin the k x w window of beta is staged once in shared memory as FP16
+ * hi + lo tensor-core fragments and a warp reconstructs 16 candidates at a time with mma.sync
+ * (three products hi.hi + hi.lo + lo.hi, FP32 accumulation), reading the coefficients that
+ * rb_pack_coeff laid out (required: basis->coeff_op).
  *   beta: [k][n/2] complex (valid half, rb_basis_filter output).  cand: [n_cand] device.
  *   trig: [capacity] output; n_trig (host). Synchronises `stream`.
- *   Errors: RB_ERR_OVERFLOW as for rb_stage1.
+ *   Errors: RB_ERR_OVERFLOW as for rb_stage1; RB_ERR_BAD_INPUT without coeff_op or with n_cand
+ *   above desc->cand_capacity.
  */
 int rb_stage2(const rb_filter_desc* desc, const rb_basis* basis, const float* beta,
               const rb_candidate* cand, int64_t n_cand, rb_trigger* trig, int64_t capacity,

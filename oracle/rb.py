@@ -19,7 +19,8 @@ Follows arXiv:2110.13115:
   when it is >= rho_II.
 * Sec. III.D, Eqs. (10)-(12): the bin average of z equals a length-n/w inverse
   DFT of the folded spectrum Omega(f') = (1/w) sum_l Q[l n/w + f'] G(l n/w + f'),
-  G(f) = sum_{r<w} exp(2 pi i f r / n) (normalisation read as in the design doc).
+  G(f) = sum_{r<w} exp(2 pi i f r / n), with the unnormalised inverse DFT of Eq. 6 (Eqs. 10-12 mix
+  normalisation conventions; this one makes the folded series equal the bin mean exactly).
 
 The basis lives in whitened coordinates g_t[j] = sqrt(4 df / S_j) h_t[j] on
 0 <= j < n/2, in which <a|b> of Eq. (1) is the Euclidean product.
