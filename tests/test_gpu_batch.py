@@ -129,6 +129,34 @@ def test_batch_blocks_vs_oracle(api, case):
     assert both >= 10
 
 
+def test_batch_fp32_wide_bins_equals_block_by_block(api, case):
+    """The same work list with the FP32 first stage and w = 16 (one basis per size reused)."""
+    wl, descs, bases, blocks = case
+    d2 = [api.make_desc(d.fs, d.n, d.k, d.n_templates, w=16, precision="fp32", rho_i=RHO_I / 1.2,
+                        rho_ii=d.rho_ii, cand_capacity=1 << 18) for d in descs]
+    for d, b in zip(d2, bases):
+        api.rb_pack_coeff(d, b)
+    try:
+        buf, nt = api.rb_filter_batch(d2, bases, blocks, capacity=1 << 20)
+        got = _key_sorted(api.triggers_numpy(buf, nt))
+        ref = []
+        for j, (bb, blk) in enumerate(zip(wl.blocks, blocks)):
+            d = d2[blk.basis]
+            dj = api.make_desc(d.fs, d.n, d.k, d.n_templates, w=16, precision="fp32", rho_i=d.rho_i,
+                               rho_ii=d.rho_ii, cand_capacity=d.cand_capacity, sample_offset=blk.sample_offset,
+                               block_id=j)
+            b2, n2 = api.rb_filter(dj, bases[blk.basis], blk.strain, blk.psd, capacity=1 << 18)
+            t = api.triggers_numpy(b2, n2)
+            ref.append(t[t["sample"] - blk.sample_offset >= bb.valid_lo])
+        ref = _key_sorted(np.concatenate(ref))
+        assert nt > 0 and len(got) == len(ref)
+        for f in ("block", "tmpl", "sample", "snr", "phase"):
+            assert np.array_equal(got[f], ref[f]), f
+    finally:
+        for d, b in zip(descs, bases):  # restore the packing the other tests use
+            api.rb_pack_coeff(d, b)
+
+
 def test_batch_rejects_bad_blocks(api, case):
     from paper_2110_13115_gb300 import _native as N
 

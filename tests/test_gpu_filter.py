@@ -246,3 +246,40 @@ def test_fft_variants_identical(api, n, w):
     assert 0 <= chosen < N.RB_FFT_VARIANTS and all(t > 0 for t in times)
     assert times[chosen] == min(times)
     api.rb_set_fft_variant(d, 0)
+
+
+def test_stage2_order_independent_and_hot_bins(api):
+    """The bucketing accepts candidates in any order, and a bin holding thousands of candidates is cut
+    into several work pieces: the triggers are bit-identical whatever the order and agree with the
+    oracle."""
+    n, k, T, w = 1 << 14, 24, 3000, 8
+    half, nb = n // 2, n // (2 * w)
+    a = _rand_coeff(T, k, 13).astype(np.complex64)
+    beta = inputs.complex_normal((k, half), 14).astype(np.complex64)
+    rng = np.random.default_rng(15)
+    hot = np.zeros(T, dtype=api.CANDIDATE_NP)  # every template in one bin: six pieces of <= 512
+    hot["tmpl"] = np.arange(T)
+    hot["bin"] = nb + 37
+    rest = np.zeros(700, dtype=api.CANDIDATE_NP)
+    rest["tmpl"] = rng.integers(0, T, 700)
+    rest["bin"] = nb + rng.integers(0, nb, 700)
+    cands = np.unique(np.concatenate([hot, rest]))
+    d = api.make_desc(1024.0, n, k, T, w=w, rho_ii=2.0, cand_capacity=1 << 14)
+    basis = api.Basis(_dev(np.zeros((k, half), np.complex64)), _dev(a), n)
+    api.rb_pack_coeff(d, basis)
+    outs = []
+    for order in (np.arange(len(cands)), rng.permutation(len(cands))):
+        c = np.ascontiguousarray(cands[order])
+        buf, nt = api.rb_stage2(d, basis, _dev(beta), _dev(c.view(np.uint8)), len(c), capacity=1 << 14)
+        outs.append(api.triggers_numpy(buf, nt))
+    for f in ("tmpl", "sample", "snr", "phase"):
+        assert np.array_equal(outs[0][f], outs[1][f]), f
+    full = np.zeros((k, n), np.complex128)
+    full[:, half:] = beta
+    oc = np.zeros(len(cands), dtype=rb.CAND_DTYPE)
+    oc["template"] = cands["tmpl"]
+    oc["bin"] = cands["bin"]
+    ref = rb.stage2(a.astype(np.complex128), full, oc, w, 2.0)
+    zr = np.abs(np.conj(a.astype(np.complex128)) @ beta.astype(np.complex128))
+    stats = compare_triggers(outs[0], ref, w, 2.0, ref_rho=zr)
+    assert stats["both"] > 500
