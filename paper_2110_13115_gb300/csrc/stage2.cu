@@ -19,6 +19,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "internal.h"
@@ -369,6 +370,10 @@ int stage2_bucket(const rb_filter_desc& d, const Geometry& g, const Workspace& w
 
 int stage2_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
                const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st) {
+  if (stage2_use_tc() && d.w <= 8) {
+    const int rc = stage2_tc_run(d, b, g, ws, beta, trig, cap, counter, st);
+    if (rc != RB_ERR_UNSUPPORTED) return rc;
+  }
   switch (d.w) {
     case 1: return launch_bins<1>(d, b, g, ws, beta, trig, cap, counter, st);
     case 2: return launch_bins<2>(d, b, g, ws, beta, trig, cap, counter, st);
@@ -388,3 +393,20 @@ int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& 
 }
 
 }  // namespace rb
+
+namespace {
+std::atomic<int> g_stage2_tc{0};
+}
+
+namespace rb {
+bool stage2_use_tc() { return g_stage2_tc.load() != 0; }
+}  // namespace rb
+
+// Host-only hook (not part of the C ABI): 1 selects the tcgen05 second stage (stage2_tc.cu) where it
+// applies (w <= 8 and the window fits shared memory); 0, the default, keeps the per-candidate
+// mma.sync kernel above, which is the faster of the two on the 10,000-template, 2^19-sample workload
+// (1.00 ms against 1.20 ms for its 3.5 M candidates).
+extern "C" int rbx_set_stage2_tc(int on) {
+  g_stage2_tc.store(on ? 1 : 0);
+  return 0;
+}

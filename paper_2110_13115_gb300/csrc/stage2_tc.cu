@@ -1,0 +1,462 @@
+// Second stage on tcgen05 tensor cores (arXiv:2110.13115 Sec. III.C second stage, Sec. III.E custom
+// kernel): for the candidates of one bin, z_t[m] = sum_k conj(a_tk) beta_k[m] over the bin's w
+// samples as one real contraction D[128 candidates][2N] = A[128][K] . B[K][2N] with
+//   A row  = [Re a_t | Im a_t] (K = 2 k16, FP16 hi and lo planes from rb_pack_coeff, in its column order)
+//   B[kk][2r] = Re beta_kk[r] / Im beta_(kk-k16)[r],  B[kk][2r+1] = Im beta_kk[r] / -Re beta_(kk-k16)[r]
+// (the first / second half of K) in FP16 hi (columns 0..N-1) and lo (columns N..2N-1), so
+// D[., 2r] + D[., N + 2r] and D[., 2r+1] + D[., N + 2r+1] are Re and Im of z at sample r.
+// Two products per K step, A_hi . [B_hi | B_lo] and A_lo . [B_hi | B_lo], with FP32 accumulation in
+// tensor memory: the split terms hi.hi + hi.lo + lo.hi (+ lo.lo), FP32-accurate.
+//
+// Persistent kernel, one CTA per SM, 416 threads, over the pieces (<= 512 candidates of one bin)
+// that the bucketing produced:
+//   warps 0-3  : coefficient producers. Per tile of 128 candidates each warp gathers the coefficient
+//                rows of its 32 candidates, K block by K block, with cp.async into an S-deep ring
+//                (S = 2..6, as many 32-KB stages as shared memory holds); S - 2 groups stay in flight.
+//                The template index of the next tile and the record of the next piece are loaded
+//                one tile ahead.
+//   warp 4     : tensor-memory allocation and the MMA issuer (one thread), two tiles in flight.
+//   warps 5-8  : epilogue: one tensor-memory lane quarter each; arg-max over the bin, rho_II, triggers.
+//   warps 9-12 : window producers: the bin's B operand (hi and lo windows side by side, 128-byte
+//                swizzled K-major), double-buffered, so a piece's window is built while the one before runs.
+// Every mbarrier wait is bounded (1 s); a timeout sets RB_FLAG_TIMEOUT and every role stops; copies
+// and products in flight are waited for (bounded) and tensor memory is freed before the CTA exits.
+//
+// Cost: each M = 128, N = 32, K = 16 product holds the tensor pipe ~64 cycles (the A slice, 4 KB, is
+// read from shared memory at ~64 B per cycle whatever N is), so the coefficient rows alone take
+// 32 cycles per candidate; the ring (<= 160 KB) covers ~1.3 us of products against ~2 us of gather
+// latency. The per-candidate mma.sync kernel, which loads the rows straight into registers, stays the
+// default second stage.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tma.cuh"
+
+namespace {
+
+using namespace rbtma;
+
+constexpr int kBM = 128;          // candidates per tile (tensor-memory lanes)
+constexpr int kKB = 64;           // K block: 64 FP16 = one 128-byte swizzled row
+constexpr int kMaxStagesA = 6;    // coefficient ring depth, at most
+constexpr int kAStageBytes = 2 * kBM * 128;
+constexpr int kThreadsTc = 416;   // 4 + 1 + 4 + 4 warps
+constexpr unsigned kFull = 0xffffffffu;
+
+struct S2Params {
+  const __half* ahi;   // [T][2 k16] coefficient planes (packed column order)
+  const __half* alo;
+  const float2* beta;  // [k][half] valid half
+  int k, k16, kp2, nkb;  // kp2 = 2 k16 rounded up to kKB, nkb = kp2 / kKB
+  int stages;            // coefficient ring depth S
+  int T;
+  int64_t half;
+  int bin0;
+  const int4* pieces;
+  const unsigned* piece_total;
+  const rb_candidate* sorted;
+  float thr2;
+  int64_t sample_offset;
+  rb_trigger* trig;
+  unsigned long long* counter;
+  int64_t cap;
+  unsigned* flags;
+  uint32_t idesc;
+};
+
+// Packed column order of rb_pack_coeff: position p = 32 q + 8 t4 + s holds column
+// (2 q + s / 4) 16 + 2 t4 + (s & 1) + 8 ((s >> 1) & 1); this is its inverse.
+__device__ __forceinline__ int packed_pos(int col) {
+  const int kc = col >> 4, jj = col & 15;
+  const int q = kc >> 1, hb = kc & 1, t4 = (jj & 7) >> 1;
+  const int s = (jj & 1) + 2 * (jj >> 3) + 4 * hb;
+  return 32 * q + 8 * t4 + s;
+}
+
+// Byte offset of element e (0..63) of row `row` in a 128-byte swizzled K-major tile.
+__device__ __forceinline__ uint32_t sw128_off(int row, int e) {
+  return (uint32_t)(row * 128 + ((((e >> 3) ^ (row & 7))) << 4) + ((e & 7) << 1));
+}
+
+// cp.async.wait_group takes an immediate: at most n (0..4) most recent groups left pending.
+__device__ __forceinline__ void wait_groups(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+  }
+}
+
+__device__ __forceinline__ int4 piece_at(const S2Params& p, unsigned i, unsigned n) {
+  return i < n ? p.pieces[i] : make_int4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ int tiles_of(const int4& pc) { return (int)(((unsigned)pc.z - (unsigned)pc.y + kBM - 1) / kBM); }
+
+template <int W, int N>
+__global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
+  static_assert(2 * W <= N, "columns");
+  constexpr int N2 = 2 * N;  // B rows: hi window in 0..N-1, lo window in N..2N-1
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t afull[kMaxStagesA], aempty[kMaxStagesA], bfull[2], bempty[2], tfull[2], tempty[2],
+      drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr uint32_t kAcc = N2;                          // tensor-memory columns of one tile
+  constexpr uint32_t kCols = 2 * kAcc < 32 ? 32 : 2 * kAcc;  // two tiles in flight
+  static_assert(kCols <= 512 && (kCols & (kCols - 1)) == 0, "tensor-memory columns");
+  const uint32_t base = (saddr(dsm) + 1023u) & ~1023u;
+  constexpr uint32_t A_PLANE = kBM * 128, A_STAGE = kAStageBytes;
+  const int S = p.stages;
+  const uint32_t b_tile = N2 * 128, b_buf = (uint32_t)p.nkb * b_tile;
+  const uint32_t a0 = base, b0 = base + S * A_STAGE;
+  uint8_t* const gen = dsm + (base - saddr(dsm));  // generic pointer to `base`
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&afull[s], 128);
+      mbar_init(&aempty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bfull[i], 128);
+      mbar_init(&bempty[i], 1);
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const unsigned npieces = *p.piece_total, grid = gridDim.x;
+  auto fail = [&]() {
+    abort_flag = 1;
+    atomicOr(p.flags, (unsigned)RB_FLAG_TIMEOUT);
+  };
+
+  if (warp < 4) {
+    // ---------------- coefficient producers
+    const int tid = threadIdx.x;  // 0..127: the candidate row of every tile
+    const int64_t p2 = 2 * (int64_t)p.k16;
+    const int depth = S - 1;      // groups committed but not yet published, at most depth - 1
+    unsigned g = 0, pub = 0;      // groups committed / published
+    auto publish = [&]() {        // the oldest unpublished group has landed: hand it to the MMA
+      fence_async_smem();
+      mbar_arrive(&afull[pub % S]);
+      ++pub;
+    };
+    auto tmpl_at = [&](const int4& pc, int tile) {
+      const unsigned ci = (unsigned)pc.y + tile * kBM + tid;
+      int t = ci < (unsigned)pc.z ? p.sorted[ci].tmpl : -1;
+      return t >= p.T ? -1 : t;
+    };
+    unsigned pc_i = blockIdx.x;
+    int4 pc = piece_at(p, pc_i, npieces), pcn = piece_at(p, pc_i + grid, npieces);
+    int tile = 0;
+    int t = pc_i < npieces ? tmpl_at(pc, 0) : -1;
+    while (pc_i < npieces && !__any_sync(kFull, abort_flag != 0)) {
+      // the next tile, and its template, before this tile's copies
+      const bool same = tile + 1 < tiles_of(pc);
+      const unsigned nx_i = same ? pc_i : pc_i + grid;
+      const int nx_tile = same ? tile + 1 : 0;
+      const int t_next = nx_i < npieces ? tmpl_at(same ? pc : pcn, nx_tile) : -1;
+      // 8 lanes per row: one warp instruction copies 4 whole 128-byte lines; the warp covers its
+      // 32 rows (its own candidates) in 8 instructions per plane
+      const __half* rowp[8];
+      bool rv[8];
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int tr = __shfl_sync(kFull, t, 4 * it + (lane >> 3));
+        rv[it] = tr >= 0;
+        rowp[it] = p.ahi + (int64_t)max(tr, 0) * p2 + (lane & 7) * 8;
+      }
+      const int64_t lo_off = (int64_t)p.T * p2;
+      bool ok = true;
+      for (int kb = 0; kb < p.nkb; ++kb, ++g) {
+        const uint32_t s = g % S, ph = (g / S) & 1;
+        // every lane waits; the outcome is made warp-uniform before the warp-wide steps below
+        if (!__all_sync(kFull, mbar_wait(&aempty[s], ph ^ 1, &abort_flag))) {
+          if (lane == 0) fail();
+          ok = false;
+          break;
+        }
+        const uint32_t dst = a0 + s * A_STAGE;
+        const int col = kb * kKB + (lane & 7) * 8;  // first FP16 element of this lane's 16-byte chunk
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const bool v = rv[it] && col < 2 * p.k16;
+          const uint32_t off = sw128_off(32 * warp + 4 * it + (lane >> 3), (lane & 7) * 8);
+          const __half* src = rowp[it] + (v ? kb * kKB : 0);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst + off), "l"(src), "r"(v ? 16 : 0)
+                       : "memory");
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst + A_PLANE + off), "l"(src + lo_off),
+                       "r"(v ? 16 : 0)
+                       : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (g + 1 - pub == (unsigned)depth) {
+          wait_groups(depth - 1);
+          publish();
+        }
+      }
+      if (!ok) break;
+      if (!same) {
+        pc = pcn;
+        pcn = piece_at(p, nx_i + grid, npieces);
+      }
+      pc_i = nx_i;
+      tile = nx_tile;
+      t = t_next;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    while (pub < g) publish();
+  } else if (warp == 4) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      unsigned g = 0, gt = 0, i = 0;
+      bool issued = false;
+      int4 pcn = piece_at(p, blockIdx.x, npieces);
+      for (unsigned pc_i = blockIdx.x; pc_i < npieces && !abort_flag; pc_i += grid, ++i) {
+        const int4 pc = pcn;
+        pcn = piece_at(p, pc_i + grid, npieces);
+        const int pb = i & 1;
+        if (!mbar_wait(&bfull[pb], (i >> 1) & 1, &abort_flag)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t bt = b0 + pb * b_buf;
+        const int ntiles = tiles_of(pc);
+        bool ok = true;
+        for (int tile = 0; tile < ntiles && ok; ++tile, ++gt) {
+          const int acc = gt & 1;
+          if (!mbar_wait(&tempty[acc], ((gt >> 1) & 1) ^ 1, &abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)acc * kAcc;
+          for (int kb = 0; kb < p.nkb; ++kb, ++g) {
+            const uint32_t s = g % S, ph = (g / S) & 1;
+            if (!mbar_wait(&afull[s], ph, &abort_flag)) {
+              fail();
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t ah = a0 + s * A_STAGE, al = ah + A_PLANE;
+            const uint32_t bk = bt + kb * b_tile;
+#pragma unroll
+            for (int kk = 0; kk < kKB / 16; ++kk) {
+              const uint32_t off = kk * 32;
+              tc_mma(d, sw128_desc(ah + off), sw128_desc(bk + off), p.idesc, (kb | kk) != 0);
+              tc_mma(d, sw128_desc(al + off), sw128_desc(bk + off), p.idesc, 1);
+            }
+            issued = true;
+            tc_commit(&aempty[s]);
+          }
+          if (!ok) break;
+          tc_commit(&tfull[acc]);
+        }
+        if (!ok) break;
+        tc_commit(&bempty[pb]);
+      }
+      if (issued) {
+        // every product issued so far has completed before tensor memory is released
+        tc_commit(&drain);
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(&drain, 0) && gtimer() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp < 9) {
+    // ---------------- epilogue: warp 5..8 reads tensor-memory lanes 32 (warp % 4) + [0, 32)
+    const int q = warp & 3;
+    unsigned gt = 0;
+    bool stop = false;
+    int4 pcn = piece_at(p, blockIdx.x, npieces);
+    for (unsigned pc_i = blockIdx.x; pc_i < npieces && !stop; pc_i += grid) {
+      const int4 pc = pcn;
+      pcn = piece_at(p, pc_i + grid, npieces);
+      const int bin = pc.x;
+      const unsigned c0 = (unsigned)pc.y, c1 = (unsigned)pc.z;
+      const int ntiles = tiles_of(pc);
+      for (int tile = 0; tile < ntiles; ++tile, ++gt) {
+        const int acc = gt & 1;
+        if (!__all_sync(kFull, mbar_wait(&tfull[acc], (gt >> 1) & 1, &abort_flag))) {
+          if (lane == 0) fail();
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        float v[32];
+        tc_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * kAcc, v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[acc]);
+        const unsigned ci = c0 + tile * kBM + q * 32 + lane;
+        float best = -1.f, zr = 0.f, zi = 0.f;
+        int br = 0;
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+          const float re = v[2 * r] + v[N + 2 * r], im = v[2 * r + 1] + v[N + 2 * r + 1];
+          const float p2s = fmaf(re, re, im * im);
+          if (p2s > best) {
+            best = p2s;
+            br = r;
+            zr = re;
+            zi = im;
+          }
+        }
+        const bool emit = ci < c1 && best >= p.thr2;
+        const unsigned em = __ballot_sync(kFull, emit);
+        if (!em) continue;
+        const int leader = __ffs(em) - 1;
+        unsigned long long b0c = 0;
+        if (lane == leader) b0c = atomicAdd(p.counter, (unsigned long long)__popc(em));
+        b0c = __shfl_sync(kFull, b0c, leader);
+        if (emit) {
+          const rb_candidate cd = p.sorted[ci];
+          const unsigned long long idx = b0c + __popc(em & ((1u << lane) - 1u));
+          if ((int64_t)idx < p.cap) {
+            rb_trigger tg;
+            tg.sample = p.sample_offset + (int64_t)(p.bin0 + bin) * W + br;
+            tg.tmpl = cd.tmpl;
+            tg.block = cd.block;
+            tg.snr = sqrtf(best);
+            tg.phase = atan2f(zi, zr);
+            p.trig[idx] = tg;
+          }
+        }
+      }
+    }
+  } else {
+    // ---------------- window producers: B operand of each piece's bin, double-buffered
+    const int tid = threadIdx.x - 9 * 32;  // 0..127
+    // zero both B buffers once: columns n >= 2W and positions >= 2 k16 are never written again
+    for (uint32_t o = tid * 16; o < 2 * b_buf; o += 128 * 16)
+      *reinterpret_cast<uint4*>(gen + (b0 - base) + o) = make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const int total = p.k16 * W;
+    int4 pcn = piece_at(p, blockIdx.x, npieces);
+    unsigned i = 0;
+    for (unsigned pc_i = blockIdx.x; pc_i < npieces && !abort_flag; pc_i += grid, ++i) {
+      const int bin = pcn.x;
+      pcn = piece_at(p, pc_i + grid, npieces);
+      const int pb = i & 1;
+      if (!mbar_wait(&bempty[pb], ((i >> 1) & 1) ^ 1, &abort_flag)) {
+        fail();
+        break;
+      }
+      const int64_t m0 = (int64_t)(p.bin0 + bin) * W - p.half;
+      uint8_t* bt = gen + (b0 - base) + pb * b_buf;
+      for (int i0 = tid; i0 < total; i0 += 4 * 128) {
+        float2 bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {  // loads first, then the stores
+          const int idx = i0 + u * 128, kk = idx / W, r = idx - kk * W;
+          bv[u] = idx < total && kk < p.k ? __ldg(p.beta + (int64_t)kk * p.half + m0 + r) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = i0 + u * 128, kk = idx / W, r = idx - kk * W;
+          if (idx >= total) break;
+          // (column, n, value): Re half at column kk, Im half at column k16 + kk
+          const float vals[4] = {bv[u].x, bv[u].y, bv[u].y, -bv[u].x};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int col = (e < 2 ? 0 : p.k16) + kk, n = 2 * r + (e & 1);
+            const int pos = packed_pos(col);
+            uint8_t* kt = bt + (uint32_t)(pos / kKB) * b_tile;
+            const __half h = __float2half_rn(vals[e]);
+            *reinterpret_cast<__half*>(kt + sw128_off(n, pos % kKB)) = h;
+            *reinterpret_cast<__half*>(kt + sw128_off(N + n, pos % kKB)) = __float2half_rn(vals[e] - __half2float(h));
+          }
+        }
+      }
+      fence_async_smem();
+      mbar_arrive(&bfull[pb]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 4) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kCols)
+                 : "memory");
+  }
+}
+
+template <int W, int N>
+int launch_tc2(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
+               const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st) {
+  S2Params p;
+  p.k16 = (int)g.k16;
+  p.k = d.k;
+  p.kp2 = (2 * p.k16 + kKB - 1) / kKB * kKB;
+  p.nkb = p.kp2 / kKB;
+  p.ahi = reinterpret_cast<const __half*>(b.coeff_op);
+  p.alo = p.ahi + (int64_t)d.n_templates * 2 * p.k16;
+  p.beta = beta;
+  p.T = d.n_templates;
+  p.half = g.n / 2;
+  p.bin0 = (int)g.n_bins;
+  p.pieces = ws.pieces;
+  p.piece_total = ws.piece_total;
+  p.sorted = ws.cand_sorted;
+  p.thr2 = d.rho_ii * d.rho_ii;
+  p.sample_offset = d.sample_offset;
+  p.trig = trig;
+  p.counter = counter;
+  p.cap = cap;
+  p.flags = ws.flags;
+  p.idesc = (1u << 4) | ((uint32_t)((2 * N) >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);  // F32 acc, FP16 A/B
+  const int b_bytes = 2 * p.nkb * 2 * N * 128, limit = 227 * 1024 - 1024 - 256;  // 256: static barriers
+  p.stages = std::min(kMaxStagesA, (limit - b_bytes) / kAStageBytes);
+  if (p.stages < 2) {
+    rb::set_detail("k = %d too large for the tensor-core second stage", d.k);
+    return RB_ERR_UNSUPPORTED;
+  }
+  const int smem = p.stages * kAStageBytes + b_bytes + 1024;
+  auto kern = k_stage2_tc<W, N>;
+  RB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  kern<<<152, kThreadsTc, smem, st>>>(p);
+  RB_LAUNCH_CHECK();
+  return RB_OK;
+}
+
+}  // namespace
+
+namespace rb {
+
+int stage2_tc_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
+                  const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st) {
+  switch (d.w) {
+    case 1: return launch_tc2<1, 16>(d, b, g, ws, beta, trig, cap, counter, st);
+    case 2: return launch_tc2<2, 16>(d, b, g, ws, beta, trig, cap, counter, st);
+    case 4: return launch_tc2<4, 16>(d, b, g, ws, beta, trig, cap, counter, st);
+    case 8: return launch_tc2<8, 16>(d, b, g, ws, beta, trig, cap, counter, st);
+  }
+  set_detail("the tensor-core second stage takes w <= 8");
+  return RB_ERR_UNSUPPORTED;
+}
+
+}  // namespace rb

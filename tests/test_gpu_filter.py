@@ -283,3 +283,51 @@ def test_stage2_order_independent_and_hot_bins(api):
     zr = np.abs(np.conj(a.astype(np.complex128)) @ beta.astype(np.complex128))
     stats = compare_triggers(outs[0], ref, w, 2.0, ref_rho=zr)
     assert stats["both"] > 500
+
+
+@pytest.mark.parametrize("w", [1, 2, 4, 8])
+@pytest.mark.parametrize("k", [24, 40, 256])
+def test_stage2_tc_parity(api, w, k):
+    """The tcgen05 second stage (tiles of 128 candidates, hi and lo windows side by side in one
+    N = 32 operand, two products per K step) against the oracle and against the mma.sync second
+    stage on the same candidates, including a hot bin of several tiles."""
+    from paper_2110_13115_gb300 import _native as N
+
+    lib = N.load()
+    n, T = 1 << 14, 700
+    half, nb = n // 2, n // (2 * w)
+    a = _rand_coeff(T, k, 31).astype(np.complex64)
+    beta = inputs.complex_normal((k, half), 32).astype(np.complex64)
+    rng = np.random.default_rng(33)
+    hot = np.zeros(T, dtype=api.CANDIDATE_NP)
+    hot["tmpl"] = np.arange(T)
+    hot["bin"] = nb + 5
+    rest = np.zeros(600, dtype=api.CANDIDATE_NP)
+    rest["tmpl"] = rng.integers(0, T, 600)
+    rest["bin"] = nb + rng.integers(0, nb, 600)
+    cands = np.unique(np.concatenate([hot, rest]))
+    rho_ii = 1.5  # unit-norm coefficients: |z| is Rayleigh-distributed with scale 1 on these beta
+    d = api.make_desc(1024.0, n, k, T, w=w, rho_ii=rho_ii, cand_capacity=1 << 14)
+    basis = api.Basis(_dev(np.zeros((k, half), np.complex64)), _dev(a), n)
+    api.rb_pack_coeff(d, basis)
+    outs = []
+    try:
+        for tc in (1, 0):
+            lib.rbx_set_stage2_tc(tc)
+            buf, nt = api.rb_stage2(d, basis, _dev(beta), _dev(cands.view(np.uint8)), len(cands), capacity=1 << 14)
+            outs.append(api.triggers_numpy(buf, nt))
+    finally:
+        lib.rbx_set_stage2_tc(0)
+    got, mma = outs
+    full = np.zeros((k, n), np.complex128)
+    full[:, half:] = beta
+    oc = np.zeros(len(cands), dtype=rb.CAND_DTYPE)
+    oc["template"] = cands["tmpl"]
+    oc["bin"] = cands["bin"]
+    ref = rb.stage2(a.astype(np.complex128), full, oc, w, rho_ii)
+    zr = np.abs(np.conj(a.astype(np.complex128)) @ beta.astype(np.complex128))
+    stats = compare_triggers(got, ref, w, rho_ii, ref_rho=zr)
+    assert stats["both"] > 100, stats
+    ref2 = np.zeros(len(mma), dtype=mf.TRIGGER_DTYPE)
+    ref2["template"], ref2["sample"], ref2["snr"], ref2["phase"] = mma["tmpl"], mma["sample"], mma["snr"], mma["phase"]
+    compare_triggers(got, ref2, w, rho_ii, ref_rho=zr)
