@@ -605,7 +605,7 @@ def main():
             roof = dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", kernel="k_stage1_tc",
                         peak_source="MEASURED_PEAKS bf16_tflops_sustained (fp16 nominal rate = bf16)",
                         issued_mma_flops_ratio=3.0 if "split" in args.precision else 1.0)
-        key, srcs = roof["kernel"], ("paper_2110_13115_gb300/csrc/gemm_tc.cu",)
+        key, srcs = roof["kernel"], ("paper_2110_13115_gb300/csrc/gemm_tc.cu", "paper_2110_13115_gb300/csrc/tma.cuh")
     else:
         byts = args.k * (half * 8 + half * 8 + nb * 8)
         achieved = byts / (stage_ms[dom] / 1e3) / 1e9

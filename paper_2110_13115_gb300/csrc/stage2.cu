@@ -33,10 +33,8 @@ constexpr unsigned kPiece = rb::kStage2Piece;  // candidates per second-stage wo
 // Bins before blo (relative to bin0) are dropped: a block whose earlier valid samples another
 // block already covers keeps only [blo, nb).
 __global__ void k_bin_count(const rb_candidate* __restrict__ cand, const unsigned long long* dev_count, int64_t cap,
-                            int bin0, int blo, int nb, unsigned* __restrict__ count, unsigned* flags) {
-  const unsigned long long found = *dev_count;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && found > (unsigned long long)cap) atomicOr(flags, (unsigned)RB_FLAG_CAND_OVERFLOW);
-  const int64_t n = (int64_t)min((unsigned long long)cap, found);
+                            int bin0, int blo, int nb, unsigned* __restrict__ count) {
+  const int64_t n = (int64_t)min((unsigned long long)cap, *dev_count);
   const int lane = threadIdx.x & 31;
   for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~int64_t(31); i0 < n;
        i0 += (int64_t)gridDim.x * blockDim.x) {
@@ -48,30 +46,60 @@ __global__ void k_bin_count(const rb_candidate* __restrict__ cand, const unsigne
   }
 }
 
+constexpr int kScanPer = 4;                  // counters per thread and tile
+constexpr int kScanTile = 1024 * kScanPer;   // bins per tile
+__host__ __device__ constexpr int spad(int x) { return x + (x >> 5); }  // conflict-free per-thread runs
+
 // Exclusive scan of count[0, nb) into start[0, nb] plus the piece list; count is reset to zero
 // (it becomes the per-bin fill cursor). A bin holding c candidates is cut into ceil(c / kPiece)
 // pieces {bin, first, end} of at most kPiece consecutive bucketed candidates, so that the
 // second stage can spread a bin with thousands of candidates over many CTAs and skips empty
 // bins entirely. Counts and piece counts are scanned together as one 64-bit value (pieces in the
-// high word). One CTA of 1024 threads walks the array in tiles of 16384 counters, each thread
-// scanning 16 consecutive ones, with a running carry between tiles.
+// high word). One CTA of 1024 threads walks the array in tiles of 4096 counters, loading the next
+// tile's counters while it processes one. Counters and start[] move with coalesced accesses
+// through shared memory; each thread scans 4 consecutive counters; the tile's pieces are written
+// one per thread (coalesced), each thread finding its piece's bin by binary search over the tile's
+// piece prefix. Also raises
+// RB_FLAG_CAND_OVERFLOW when the first stage found more candidates than the buffer holds.
 __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count, unsigned* __restrict__ start, int nb,
-                                                   int4* __restrict__ pieces, unsigned* __restrict__ piece_total) {
+                                                   int4* __restrict__ pieces, unsigned* __restrict__ piece_total,
+                                                   const unsigned long long* dev_count, int64_t cap,
+                                                   unsigned* flags) {
   using u64 = unsigned long long;
-  constexpr int PER = 16;  // counters per thread: one tile covers 16384 bins
+  __shared__ unsigned st_s[spad(kScanTile) + 1];  // global start of every bin of the tile (+ the end)
+  __shared__ unsigned pp_s[spad(kScanTile) + 1];  // global index of every bin's first piece (+ the end)
   __shared__ u64 wsum[32];
-  __shared__ u64 carry_s;
+  __shared__ u64 carry_s, carry_next;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   auto packed = [](unsigned c) { return (u64)c | ((u64)((c + kPiece - 1) / kPiece) << 32); };
-  if (tid == 0) carry_s = 0;
+  if (tid == 0) {
+    carry_s = 0;
+    if (*dev_count > (u64)cap) atomicOr(flags, (unsigned)RB_FLAG_CAND_OVERFLOW);
+  }
+  unsigned nx[kScanPer];  // the next tile's counters, loaded one tile ahead (and reset)
+  auto fetch = [&](int b0) {
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+      const int i = b0 + j * 1024 + tid;
+      nx[j] = 0;
+      if (i < nb) {
+        nx[j] = count[i];
+        count[i] = 0;
+      }
+    }
+  };
+  fetch(0);
   __syncthreads();
-  for (int base = 0; base < nb; base += 1024 * PER) {
-    unsigned v[PER];
+  for (int base = 0; base < nb; base += kScanTile) {
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) st_s[spad(j * 1024 + tid)] = nx[j];
+    fetch(base + kScanTile);
+    __syncthreads();
+    unsigned v[kScanPer];
     u64 s = 0;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      const int i = base + tid * PER + j;
-      v[j] = i < nb ? count[i] : 0u;
+    for (int j = 0; j < kScanPer; ++j) {
+      v[j] = st_s[spad(tid * kScanPer + j)];
       s += packed(v[j]);
     }
     u64 inc = s;
@@ -95,19 +123,37 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
     __syncthreads();
     u64 run = carry_s + wsum[warp] + inc - s;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      const int i = base + tid * PER + j;
-      if (i < nb) {
-        const unsigned c0 = (unsigned)run, c = v[j], p0 = (unsigned)(run >> 32);
-        start[i] = c0;
-        count[i] = 0;
-        for (unsigned q = 0; q * kPiece < c; ++q)
-          pieces[p0 + q] = make_int4(i, (int)(c0 + q * kPiece), (int)(c0 + min(c, (q + 1) * kPiece)), 0);
-      }
+    for (int j = 0; j < kScanPer; ++j) {
+      const int x = tid * kScanPer + j;
+      st_s[spad(x)] = (unsigned)run;
+      pp_s[spad(x)] = (unsigned)(run >> 32);
       run += packed(v[j]);
     }
+    if (tid == 1023) {  // bins past nb count 0, so this is the tile's end
+      st_s[spad(kScanTile)] = (unsigned)run;
+      pp_s[spad(kScanTile)] = (unsigned)(run >> 32);
+      carry_next = run;
+    }
     __syncthreads();
-    if (tid == 1023) carry_s = run;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+      const int x = j * 1024 + tid, i = base + x;
+      if (i < nb) start[i] = st_s[spad(x)];
+    }
+    const unsigned p_end = (unsigned)(carry_next >> 32);
+    for (unsigned pi = (unsigned)(carry_s >> 32) + tid; pi < p_end; pi += 1024) {
+      int lo = 0, hi = kScanTile;  // pp[lo] <= pi < pp[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pp_s[spad(mid)] <= pi) lo = mid;
+        else hi = mid;
+      }
+      const unsigned c0 = st_s[spad(lo)] + (pi - pp_s[spad(lo)]) * kPiece;
+      const unsigned c1 = min(st_s[spad(lo + 1)], c0 + kPiece);
+      pieces[pi] = make_int4(base + lo, (int)c0, (int)c1, 0);
+    }
+    __syncthreads();
+    if (tid == 0) carry_s = carry_next;
     __syncthreads();
   }
   if (tid == 0) {
@@ -116,28 +162,42 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
   }
 }
 
+// Candidates into bin order: 4 consecutive groups of 32 per warp and pass, so that the loads, the
+// per-bin cursor atomics and the stores of the 4 groups overlap.
 __global__ void k_bin_scatter(const rb_candidate* __restrict__ cand, const unsigned long long* dev_count, int64_t cap,
                               int bin0, int blo, int nb, const unsigned* __restrict__ start,
                               unsigned* __restrict__ cursor,
                               rb_candidate* __restrict__ out) {
+  constexpr int U = 4;
   const int64_t n = (int64_t)min((unsigned long long)cap, *dev_count);
   const int lane = threadIdx.x & 31;
-  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~int64_t(31); i0 < n;
-       i0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = i0 + lane;
-    rb_candidate c;
-    int b = -1;
-    if (i < n) {
-      c = cand[i];
-      b = c.bin - bin0;
-      if (b < blo || b >= nb) b = -1;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp0 * (32 * U); base < n; base += nwarps * (32 * U)) {
+    rb_candidate c[U];
+    int b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * 32 + lane;
+      b[u] = -1;
+      if (i < n) {
+        c[u] = cand[i];
+        b[u] = c[u].bin - bin0;
+        if (b[u] < blo || b[u] >= nb) b[u] = -1;
+      }
     }
-    const unsigned peers = __match_any_sync(kFull, b);
-    const int leader = __ffs(peers) - 1;
-    unsigned pos = 0;
-    if (b >= 0 && lane == leader) pos = atomicAdd(cursor + b, (unsigned)__popc(peers));
-    pos = __shfl_sync(kFull, pos, leader);
-    if (b >= 0) out[start[b] + pos + __popc(peers & ((1u << lane) - 1u))] = c;
+    unsigned peers[U], pos[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      peers[u] = __match_any_sync(kFull, b[u]);
+      pos[u] = 0;
+      if (b[u] >= 0 && lane == __ffs(peers[u]) - 1) pos[u] = atomicAdd(cursor + b[u], (unsigned)__popc(peers[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const unsigned p = __shfl_sync(kFull, pos[u], __ffs(peers[u]) - 1);
+      if (b[u] >= 0) out[start[b[u]] + p + __popc(peers[u] & ((1u << lane) - 1u))] = c[u];
+    }
   }
 }
 
@@ -357,10 +417,10 @@ int stage2_bucket(const rb_filter_desc& d, const Geometry& g, const Workspace& w
   const int nb = (int)g.n_bins;
   const int bin0 = nb;  // valid bins are [n/(2w), n/w)
   RB_CUDA_TRY(cudaMemsetAsync(ws.bin_count, 0, sizeof(unsigned) * (nb + 1), st));
-  k_bin_count<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb,
-                                       ws.bin_count, ws.flags);
+  k_bin_count<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, ws.bin_count);
   RB_LAUNCH_CHECK();
-  k_bin_scan<<<1, 1024, 0, st>>>(ws.bin_count, ws.bin_start, nb, ws.pieces, ws.piece_total);
+  k_bin_scan<<<1, 1024, 0, st>>>(ws.bin_count, ws.bin_start, nb, ws.pieces, ws.piece_total, ws.cand_count,
+                                 d.cand_capacity, ws.flags);
   RB_LAUNCH_CHECK();
   k_bin_scatter<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, ws.bin_start,
                                          ws.bin_count, ws.cand_sorted);
