@@ -293,6 +293,37 @@ def cufft_comparator(torch, templates, s_hat, n, w, rho_ii, secs, sample=512, ch
                 sample_templates=sample)
 
 
+def cufft_basis_filter(torch, vectors, s_hat, n, w, chunk=16, reps=3):
+    """The basis filter (a2 + a3) with library calls on the same GPU: per chunk of basis vectors the
+    elementwise product with the whitened data, a cuFFT inverse transform (torch.fft), the copy of
+    the valid half and the bin average. Timed only; returns its time per block in ms."""
+    k, half = vectors.shape[0], n // 2
+    q = torch.zeros((chunk, n), dtype=torch.complex64, device="cuda")
+    beta = torch.empty((k, half), dtype=torch.complex64, device="cuda")
+    bavg = torch.empty((k, half // w), dtype=torch.complex64, device="cuda")
+
+    def run():
+        for c0 in range(0, k, chunk):
+            c = min(chunk, k - c0)
+            q[:c, :half] = s_hat[None, :] * vectors[c0:c0 + c].conj()
+            z = torch.fft.ifft(q[:c], dim=1, norm="forward")
+            beta[c0:c0 + c] = z[:, half:]
+            bavg[c0:c0 + c] = z[:, half:].reshape(c, -1, w).mean(dim=2)
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del q, beta, bavg
+    return dict(ms=ms, impl="torch.fft (cuFFT) inverse FFT per basis vector + product, valid-half copy, bin average",
+                chunk=chunk)
+
+
 def run_batch(args):
     """Batch workload: 64 segments of 32-512 s at 2048 Hz seen by two detectors (independent Gaussian
     noise, PSD scale factors 0.5-2), blocks of min(128 s, 2^floor(log2 L)) with half overlap (FFT sizes
@@ -568,6 +599,9 @@ def main():
         cufft = cufft_comparator(torch, templates, sh_c, g.n, args.w, wl.rho_ii, secs_per_block)
         cufft["speedup"] = value / cufft["value"]
         plain["cufft"] = cufft
+        cbf = cufft_basis_filter(torch, basis.vectors, sh_c, g.n, args.w)
+        cbf["speedup"] = cbf["ms"] / stage_ms["basis_filter"]
+        plain["cufft_basis_filter"] = cbf
         del sh_c
 
     # roofline of the dominant stage

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -29,20 +30,64 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kPiece = rb::kStage2Piece;  // candidates per second-stage work item
 
-// Per-bin counts; lanes holding the same bin combine into one atomic.
-// Bins before blo (relative to bin0) are dropped: a block whose earlier valid samples another
-// block already covers keeps only [blo, nb).
-__global__ void k_bin_count(const rb_candidate* __restrict__ cand, const unsigned long long* dev_count, int64_t cap,
-                            int bin0, int blo, int nb, unsigned* __restrict__ count) {
+// Bucketing works on chunks of consecutive candidates. The first stage emits candidates in tile
+// order and the tiles in flight share their bins, so a chunk's bins lie in a narrow range: each CTA
+// histograms its chunk in shared memory over a window of kWin bins from the chunk's smallest bin and
+// then issues one global atomic per (chunk, bin) instead of one per candidate. Bins outside the
+// window (candidate lists in any other order) take one global atomic each.
+constexpr int kWin = 4096;  // histogram window (bins)
+
+__device__ __forceinline__ int block_min(int v, int* red) {  // blockDim.x == 256
+  v = __reduce_min_sync(kFull, v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int m = red[0];
+#pragma unroll
+  for (int i = 1; i < 8; ++i) m = min(m, red[i]);
+  return m;
+}
+
+// Per-bin counts of the candidates [0, min(cap, count)) whose bin (relative to bin0) lies in
+// [blo, nb): bins before blo are dropped, as a block whose earlier valid samples another block
+// already covers keeps only [blo, nb). 256 threads, chunks of 4096 candidates.
+__global__ void __launch_bounds__(256) k_bin_count(const rb_candidate* __restrict__ cand,
+                                                   const unsigned long long* dev_count, int64_t cap, int bin0,
+                                                   int blo, int nb, unsigned* __restrict__ count) {
+  constexpr int PER = 16, CHUNK = 256 * PER;
+  __shared__ unsigned hist[kWin];
+  __shared__ int red[8];
   const int64_t n = (int64_t)min((unsigned long long)cap, *dev_count);
-  const int lane = threadIdx.x & 31;
-  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~int64_t(31); i0 < n;
-       i0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = i0 + lane;
-    int b = i < n ? cand[i].bin - bin0 : -1;
-    if (b < blo || b >= nb) b = -1;
-    const unsigned peers = __match_any_sync(kFull, b);
-    if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(count + b, (unsigned)__popc(peers));
+  const int tid = threadIdx.x;
+  for (int64_t c0 = blockIdx.x * (int64_t)CHUNK; c0 < n; c0 += (int64_t)gridDim.x * CHUNK) {
+    int b[PER];
+    int mn = INT_MAX;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int64_t i = c0 + j * 256 + tid;
+      b[j] = -1;
+      if (i < n) {
+        const int x = cand[i].bin - bin0;
+        if (x >= blo && x < nb) b[j] = x;
+      }
+      if (b[j] >= 0) mn = min(mn, b[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kWin / 256; ++j) hist[j * 256 + tid] = 0u;
+    const int lo = block_min(mn, red);  // (its __syncthreads also orders the zeroing)
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      if (b[j] < 0) continue;
+      const int d = b[j] - lo;
+      if (d < kWin) atomicAdd(&hist[d], 1u);
+      else atomicAdd(count + b[j], 1u);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kWin / 256; ++j) {
+      const unsigned h = hist[j * 256 + tid];
+      if (h) atomicAdd(count + lo + j * 256 + tid, h);
+    }
+    __syncthreads();  // hist and red are reused by the next chunk
   }
 }
 
@@ -162,42 +207,59 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
   }
 }
 
-// Candidates into bin order: 4 consecutive groups of 32 per warp and pass, so that the loads, the
-// per-bin cursor atomics and the stores of the 4 groups overlap.
-__global__ void k_bin_scatter(const rb_candidate* __restrict__ cand, const unsigned long long* dev_count, int64_t cap,
-                              int bin0, int blo, int nb, const unsigned* __restrict__ start,
-                              unsigned* __restrict__ cursor,
-                              rb_candidate* __restrict__ out) {
-  constexpr int U = 4;
+// Candidates into bin order, by chunks of 2048 (256 threads): a candidate's rank among the chunk's
+// candidates of its bin comes from a shared-memory atomic, the chunk's base in the bin from one
+// global cursor atomic per (chunk, bin); bins outside the window take one global atomic each.
+__global__ void __launch_bounds__(256) k_bin_scatter(const rb_candidate* __restrict__ cand,
+                                                     const unsigned long long* dev_count, int64_t cap, int bin0,
+                                                     int blo, int nb, const unsigned* __restrict__ start,
+                                                     unsigned* __restrict__ cursor,
+                                                     rb_candidate* __restrict__ out) {
+  constexpr int PER = 8, CHUNK = 256 * PER;
+  __shared__ unsigned hist[kWin];
+  __shared__ int red[8];
   const int64_t n = (int64_t)min((unsigned long long)cap, *dev_count);
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp0 * (32 * U); base < n; base += nwarps * (32 * U)) {
-    rb_candidate c[U];
-    int b[U];
+  const int tid = threadIdx.x;
+  for (int64_t c0 = blockIdx.x * (int64_t)CHUNK; c0 < n; c0 += (int64_t)gridDim.x * CHUNK) {
+    rb_candidate c[PER];
+    int b[PER];
+    int mn = INT_MAX;
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t i = base + u * 32 + lane;
-      b[u] = -1;
+    for (int j = 0; j < PER; ++j) {
+      const int64_t i = c0 + j * 256 + tid;
+      b[j] = -1;
       if (i < n) {
-        c[u] = cand[i];
-        b[u] = c[u].bin - bin0;
-        if (b[u] < blo || b[u] >= nb) b[u] = -1;
+        c[j] = cand[i];
+        const int x = c[j].bin - bin0;
+        if (x >= blo && x < nb) b[j] = x;
       }
-    }
-    unsigned peers[U], pos[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      peers[u] = __match_any_sync(kFull, b[u]);
-      pos[u] = 0;
-      if (b[u] >= 0 && lane == __ffs(peers[u]) - 1) pos[u] = atomicAdd(cursor + b[u], (unsigned)__popc(peers[u]));
+      if (b[j] >= 0) mn = min(mn, b[j]);
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const unsigned p = __shfl_sync(kFull, pos[u], __ffs(peers[u]) - 1);
-      if (b[u] >= 0) out[start[b[u]] + p + __popc(peers[u] & ((1u << lane) - 1u))] = c[u];
+    for (int j = 0; j < kWin / 256; ++j) hist[j * 256 + tid] = 0u;
+    const int lo = block_min(mn, red);
+    unsigned r[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      r[j] = 0;
+      if (b[j] >= 0 && b[j] - lo < kWin) r[j] = atomicAdd(&hist[b[j] - lo], 1u);
     }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kWin / 256; ++j) {  // the chunk's base position inside each bin
+      const int x = j * 256 + tid;
+      const unsigned h = hist[x];
+      if (h) hist[x] = atomicAdd(cursor + lo + x, h);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      if (b[j] < 0) continue;
+      const int d = b[j] - lo;
+      const unsigned pos = d < kWin ? hist[d] + r[j] : atomicAdd(cursor + b[j], 1u);
+      out[start[b[j]] + pos] = c[j];
+    }
+    __syncthreads();  // hist and red are reused by the next chunk
   }
 }
 
