@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--segments", type=int, default=64, help="segments of the batch workload")
     p.add_argument("--fft-variant", type=int, default=None, help="pin the FFT schedule (skips its tuning)")
     p.add_argument("--stage1-variant", type=int, default=None, help="pin the first-stage tile (skips its tuning)")
+    p.add_argument("--stage2", default="mma", choices=["mma", "tc"],
+                   help="second-stage kernel: per-candidate mma.sync (default) or the tcgen05 kernel (w <= 8)")
     return p.parse_args()
 
 
@@ -477,7 +479,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2110_13115_gb300 import api, _native, replicas
 
-    _native.load()
+    _native.load().rbx_set_stage2_tc(1 if args.stage2 == "tc" else 0)
     g = wl.grid
     T = len(wl.bank)
     psd_d = torch.from_numpy(wl.psd).cuda()
@@ -634,10 +636,16 @@ def main():
         del sh_n, bavg_n
         flops = 8.0 * args.k * args.w * n_cand
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
-        roof = dict(bound="tensor", achieved=achieved, peak=tensor, unit="TFLOP/s", kernel="k_stage2_bins",
-                    peak_source="MEASURED_PEAKS bf16_tflops_sustained (the kernel issues mma.sync FP16, 3 products)",
-                    issued_mma_flops_ratio=3.0, candidates=int(n_cand))
-        key, srcs = roof["kernel"], ("paper_2110_13115_gb300/csrc/stage2.cu",)
+        if args.stage2 == "tc":
+            roof = dict(bound="tensor", achieved=achieved, peak=tensor, unit="TFLOP/s", kernel="k_stage2_tc",
+                        peak_source="MEASURED_PEAKS bf16_tflops_sustained (tcgen05 FP16, 2 products of N = 32)",
+                        issued_mma_flops_ratio=4.0, candidates=int(n_cand))
+            key, srcs = roof["kernel"], ("paper_2110_13115_gb300/csrc/stage2_tc.cu", "paper_2110_13115_gb300/csrc/tma.cuh")
+        else:
+            roof = dict(bound="tensor", achieved=achieved, peak=tensor, unit="TFLOP/s", kernel="k_stage2_bins",
+                        peak_source="MEASURED_PEAKS bf16_tflops_sustained (the kernel issues mma.sync FP16, 3 products)",
+                        issued_mma_flops_ratio=3.0, candidates=int(n_cand))
+            key, srcs = roof["kernel"], ("paper_2110_13115_gb300/csrc/stage2.cu",)
     elif dom == "first_stage":
         flops = 8.0 * T * args.k * nb
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
@@ -678,6 +686,7 @@ def main():
                            rho_I_calibration=f"noise-only block, {n_cal} flat triggers, recovery {args.recovery}",
                            l2="inputs larger than L2: the basis alone is 537 MB per step",
                            first_stage_tile=tuned, fft_schedule=fft_tuned,
+                           second_stage={"mma": "mma.sync", "tc": "tcgen05"}[args.stage2],
                            parallelism=f"replicas x{world} (one block per GPU)"),
                roofline=roof, cpu_baseline=cpu,
                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h_total // args.steps,

@@ -527,7 +527,7 @@ bool stage2_use_tc() { return g_stage2_tc.load() != 0; }
 // Host-only hook (not part of the C ABI): 1 selects the tcgen05 second stage (stage2_tc.cu) where it
 // applies (w <= 8 and the window fits shared memory); 0, the default, keeps the per-candidate
 // mma.sync kernel above, which is the faster of the two on the 10,000-template, 2^19-sample workload
-// (1.00 ms against 1.20 ms for its 3.5 M candidates).
+// (1.00 ms against 1.13 ms for its 3.5 M candidates).
 extern "C" int rbx_set_stage2_tc(int on) {
   g_stage2_tc.store(on ? 1 : 0);
   return 0;

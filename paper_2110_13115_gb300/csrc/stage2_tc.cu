@@ -12,7 +12,8 @@
 // that the bucketing produced:
 //   warps 0-3  : coefficient producers. Per tile of 128 candidates each warp gathers the coefficient
 //                rows of its 32 candidates, K block by K block, with cp.async into an S-deep ring
-//                (S = 2..6, as many 32-KB stages as shared memory holds); S - 2 groups stay in flight.
+//                (S = 2..6, as many 32-KB stages as shared memory holds); a stage is published to the
+//                MMA by cp.async.mbarrier.arrive when its copies land, so no producer waits on them.
 //                The template index of the next tile and the record of the next piece are loaded
 //                one tile ahead.
 //   warp 4     : tensor-memory allocation and the MMA issuer (one thread), two tiles in flight.
@@ -22,11 +23,11 @@
 // Every mbarrier wait is bounded (1 s); a timeout sets RB_FLAG_TIMEOUT and every role stops; copies
 // and products in flight are waited for (bounded) and tensor memory is freed before the CTA exits.
 //
-// Cost: each M = 128, N = 32, K = 16 product holds the tensor pipe ~64 cycles (the A slice, 4 KB, is
-// read from shared memory at ~64 B per cycle whatever N is), so the coefficient rows alone take
-// 32 cycles per candidate; the ring (<= 160 KB) covers ~1.3 us of products against ~2 us of gather
-// latency. The per-candidate mma.sync kernel, which loads the rows straight into registers, stays the
-// default second stage.
+// Cost: an M = 128, N = 32, K = 16 product takes ~16 tensor cycles, so the tensor pipe is ~10 % busy;
+// what bounds the kernel is the round trip of a ring stage (coefficient gather from L2, then the
+// products' completion) against the <= 160 KB that shared memory leaves for the ring. On the
+// 10,000-template, 2^19-sample workload (3.5 M candidates) it takes 1.13 ms, the per-candidate
+// mma.sync kernel, which loads the rows straight into registers, 1.00 ms: that one stays the default.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -81,15 +82,10 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int e) {
   return (uint32_t)(row * 128 + ((((e >> 3) ^ (row & 7))) << 4) + ((e & 7) << 1));
 }
 
-// cp.async.wait_group takes an immediate: at most n (0..4) most recent groups left pending.
-__device__ __forceinline__ void wait_groups(int n) {
-  switch (n) {
-    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
-  }
+// One arrival on `bar` once every cp.async this thread issued so far has landed (the barrier's
+// expected count includes it); the thread itself does not wait.
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(bar)) : "memory");
 }
 
 __device__ __forceinline__ int4 piece_at(const S2Params& p, unsigned i, unsigned n) {
@@ -154,13 +150,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
     // ---------------- coefficient producers
     const int tid = threadIdx.x;  // 0..127: the candidate row of every tile
     const int64_t p2 = 2 * (int64_t)p.k16;
-    const int depth = S - 1;      // groups committed but not yet published, at most depth - 1
-    unsigned g = 0, pub = 0;      // groups committed / published
-    auto publish = [&]() {        // the oldest unpublished group has landed: hand it to the MMA
-      fence_async_smem();
-      mbar_arrive(&afull[pub % S]);
-      ++pub;
-    };
+    unsigned g = 0;  // K blocks issued so far
     auto tmpl_at = [&](const int4& pc, int tile) {
       const unsigned ci = (unsigned)pc.y + tile * kBM + tid;
       int t = ci < (unsigned)pc.z ? p.sorted[ci].tmpl : -1;
@@ -209,11 +199,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
                        "r"(v ? 16 : 0)
                        : "memory");
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        if (g + 1 - pub == (unsigned)depth) {
-          wait_groups(depth - 1);
-          publish();
-        }
+        cp_async_arrive(&afull[s]);  // the stage is published when its copies land
       }
       if (!ok) break;
       if (!same) {
@@ -225,7 +211,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
       t = t_next;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
-    while (pub < g) publish();
   } else if (warp == 4) {
     // ---------------- MMA issuer
     if (lane == 0) {
@@ -261,6 +246,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
               break;
             }
             tc_fence_after();
+            fence_async_smem();  // the stage's cp.async (generic proxy) writes before the products read it
             const uint32_t ah = a0 + s * A_STAGE, al = ah + A_PLANE;
             const uint32_t bk = bt + kb * b_tile;
 #pragma unroll
