@@ -285,6 +285,45 @@ def test_stage2_order_independent_and_hot_bins(api):
     assert stats["both"] > 500
 
 
+def test_bucketing_window_and_fallback(api):
+    """Bucketing histograms each chunk of consecutive candidates over a 4096-bin window from the
+    chunk's smallest bin; bins beyond it take the per-candidate path. With 8192 valid bins, candidates
+    in bin order keep every chunk inside its window, a random order sends about half of each chunk's
+    candidates down the other path: both orders give bit-identical triggers, which agree with the
+    oracle."""
+    n, k, T, w = 1 << 17, 24, 2000, 8
+    half, nb = n // 2, n // (2 * w)
+    assert nb == 8192
+    a = _rand_coeff(T, k, 41).astype(np.complex64)
+    beta = inputs.complex_normal((k, half), 42).astype(np.complex64)
+    rng = np.random.default_rng(43)
+    cands = np.zeros(12000, dtype=api.CANDIDATE_NP)
+    cands["tmpl"] = rng.integers(0, T, len(cands))
+    cands["bin"] = nb + rng.integers(0, nb, len(cands))
+    cands = np.unique(cands)
+    d = api.make_desc(1024.0, n, k, T, w=w, rho_ii=2.0, cand_capacity=1 << 15)
+    basis = api.Basis(_dev(np.zeros((k, half), np.complex64)), _dev(a), n)
+    api.rb_pack_coeff(d, basis)
+    by_bin = np.argsort(cands["bin"], kind="stable")
+    outs = []
+    for order in (by_bin, rng.permutation(len(cands))):
+        c = np.ascontiguousarray(cands[order])
+        buf, nt = api.rb_stage2(d, basis, _dev(beta), _dev(c.view(np.uint8)), len(c), capacity=1 << 15)
+        outs.append(api.triggers_numpy(buf, nt))
+    assert len(outs[0]) == len(outs[1])
+    for f in ("tmpl", "sample", "snr", "phase"):
+        assert np.array_equal(outs[0][f], outs[1][f]), f
+    full = np.zeros((k, n), np.complex128)
+    full[:, half:] = beta
+    oc = np.zeros(len(cands), dtype=rb.CAND_DTYPE)
+    oc["template"] = cands["tmpl"]
+    oc["bin"] = cands["bin"]
+    ref = rb.stage2(a.astype(np.complex128), full, oc, w, 2.0)
+    zr = np.abs(np.conj(a.astype(np.complex128)) @ beta.astype(np.complex128))
+    stats = compare_triggers(outs[0], ref, w, 2.0, ref_rho=zr)
+    assert stats["both"] > 1000
+
+
 @pytest.mark.parametrize("w", [1, 2, 4, 8])
 @pytest.mark.parametrize("k", [24, 40, 256])
 def test_stage2_tc_parity(api, w, k):
