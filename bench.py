@@ -125,7 +125,8 @@ def run_reference(args):
     g = wl.grid
     pool = ctx.Pool(cores, initializer=_oracle_init,
                     initargs=(wl.strain, wl.psd, g.fs, g.n, g.f_low, wl.bank_spec.pn_order, wl.w, wl.rho_ii, wl.bank))
-    per_step = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
+    # about 5 x --cpu-seconds of oracle work in all (60 s by default), split over the steps
+    per_step = max(0.2, 5.0 * args.cpu_seconds / max(args.steps + args.warmup, 1))
     rates = []
     with pool:
         for i in range(args.warmup + args.steps):
