@@ -194,7 +194,8 @@ int rb_stage1(const rb_filter_desc* desc, const rb_basis* basis, const float* be
  *   beta: [k][n/2] complex (valid half, rb_basis_filter output).  cand: [n_cand] device.
  *   trig: [capacity] output; n_trig (host). Synchronises `stream`.
  *   Errors: RB_ERR_OVERFLOW as for rb_stage1; RB_ERR_BAD_INPUT without coeff_op or with n_cand
- *   above desc->cand_capacity.
+ *   above desc->cand_capacity; RB_ERR_TIMEOUT when a bounded device wait of the (opt-in) tcgen05
+ *   second stage gave up.
  */
 int rb_stage2(const rb_filter_desc* desc, const rb_basis* basis, const float* beta,
               const rb_candidate* cand, int64_t n_cand, rb_trigger* trig, int64_t capacity,

@@ -130,6 +130,7 @@ HOST_HOOKS = {
     "rbx_cholesky": (C.c_int, [C.c_int, _P, _P]),
     "rbx_stage1_withhold_copies": (C.c_int, [C.c_int]),
     "rbx_set_stage2_tc": (C.c_int, [C.c_int]),
+    "rbx_stage2_withhold_copies": (C.c_int, [C.c_int]),
 }
 
 _lib = None

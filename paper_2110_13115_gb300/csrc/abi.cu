@@ -346,7 +346,7 @@ int batch_status(const BatchSpec& s, int64_t* n_trig, cudaStream_t st) {
     return RB_ERR_BAD_INPUT;
   }
   if (stt.flags & RB_FLAG_TIMEOUT) {
-    set_detail("a device-side wait of the first stage timed out");
+    set_detail("a bounded device-side wait (tcgen05 first or second stage) timed out");
     return RB_ERR_TIMEOUT;
   }
   if (stt.flags & RB_FLAG_CAND_OVERFLOW) {
@@ -613,6 +613,10 @@ int rb_stage2(const rb_filter_desc* desc, const rb_basis* basis, const float* be
   Status s;
   if ((rc = read_status(ws, &s, st))) return rc;
   *n_trig = (int64_t)s.trig;
+  if (s.flags & RB_FLAG_TIMEOUT) {
+    set_detail("a bounded device-side wait of the tcgen05 second stage timed out");
+    return RB_ERR_TIMEOUT;
+  }
   return (int64_t)s.trig > capacity ? RB_ERR_OVERFLOW : RB_OK;
 }
 
@@ -651,7 +655,7 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
     return RB_ERR_BAD_INPUT;
   }
   if (s.flags & RB_FLAG_TIMEOUT) {
-    set_detail("a device-side wait of the first stage timed out");
+    set_detail("a bounded device-side wait (tcgen05 first or second stage) timed out");
     return RB_ERR_TIMEOUT;
   }
   if ((int64_t)s.cand > desc->cand_capacity) {

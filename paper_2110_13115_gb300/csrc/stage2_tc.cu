@@ -31,6 +31,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "internal.h"
@@ -66,6 +67,7 @@ struct S2Params {
   int64_t cap;
   unsigned* flags;
   uint32_t idesc;
+  int withhold_copies;  // failure-detection test: the producers issue no copy (rbx_stage2_withhold_copies)
 };
 
 // Packed column order of rb_pack_coeff: position p = 32 q + 8 t4 + s holds column
@@ -160,7 +162,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
     int4 pc = piece_at(p, pc_i, npieces), pcn = piece_at(p, pc_i + grid, npieces);
     int tile = 0;
     int t = pc_i < npieces ? tmpl_at(pc, 0) : -1;
-    while (pc_i < npieces && !__any_sync(kFull, abort_flag != 0)) {
+    // (withhold_copies: no copy and no arrival at all, so the MMA thread's first wait runs out)
+    while (pc_i < npieces && !p.withhold_copies && !__any_sync(kFull, abort_flag != 0)) {
       // the next tile, and its template, before this tile's copies
       const bool same = tile + 1 < tiles_of(pc);
       const unsigned nx_i = same ? pc_i : pc_i + grid;
@@ -393,7 +396,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
 
 template <int W, int N>
 int launch_tc2(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
-               const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st) {
+               const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st,
+               int withhold) {
   S2Params p;
   p.k16 = (int)g.k16;
   p.k = d.k;
@@ -414,6 +418,7 @@ int launch_tc2(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g
   p.counter = counter;
   p.cap = cap;
   p.flags = ws.flags;
+  p.withhold_copies = withhold;
   p.idesc = (1u << 4) | ((uint32_t)((2 * N) >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);  // F32 acc, FP16 A/B
   const int b_bytes = 2 * p.nkb * 2 * N * 128, limit = 227 * 1024 - 1024 - 256;  // 256: static barriers
   p.stages = std::min(kMaxStagesA, (limit - b_bytes) / kAStageBytes);
@@ -429,20 +434,34 @@ int launch_tc2(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g
   return RB_OK;
 }
 
+std::atomic<int> g_withhold2{0};  // launches left whose producers issue no copy (failure-detection test)
+
 }  // namespace
 
 namespace rb {
 
 int stage2_tc_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
                   const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st) {
+  int left = g_withhold2.load();
+  while (left > 0 && !g_withhold2.compare_exchange_weak(left, left - 1)) {
+  }
+  const int withhold = left > 0 ? 1 : 0;
   switch (d.w) {
-    case 1: return launch_tc2<1, 16>(d, b, g, ws, beta, trig, cap, counter, st);
-    case 2: return launch_tc2<2, 16>(d, b, g, ws, beta, trig, cap, counter, st);
-    case 4: return launch_tc2<4, 16>(d, b, g, ws, beta, trig, cap, counter, st);
-    case 8: return launch_tc2<8, 16>(d, b, g, ws, beta, trig, cap, counter, st);
+    case 1: return launch_tc2<1, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold);
+    case 2: return launch_tc2<2, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold);
+    case 4: return launch_tc2<4, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold);
+    case 8: return launch_tc2<8, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold);
   }
   set_detail("the tensor-core second stage takes w <= 8");
   return RB_ERR_UNSUPPORTED;
 }
 
 }  // namespace rb
+
+// Host-only test hook (not part of the C ABI): the next n tcgen05 second-stage launches issue no
+// coefficient copies, so the MMA thread's bounded wait runs out; the call reports RB_ERR_TIMEOUT and
+// the context stays usable. Used by the failure-detection test; no other code calls it.
+extern "C" int rbx_stage2_withhold_copies(int n) {
+  g_withhold2.store(n > 0 ? n : 0);
+  return 0;
+}

@@ -61,3 +61,47 @@ def test_bounded_wait_reports_timeout_and_context_survives(api):
     assert n2 == n_ref
     assert np.array_equal(got["tmpl"], ref["tmpl"]) and np.array_equal(got["bin"], ref["bin"])
     np.testing.assert_array_equal(got["snr_avg"], ref["snr_avg"])
+
+
+def test_stage2_tc_bounded_wait_reports_timeout(api):
+    """The same for the tcgen05 second stage: with its coefficient producers withholding every copy the
+    MMA thread's first wait runs out, rb_stage2 reports RB_ERR_TIMEOUT, and the next call matches."""
+    from paper_2110_13115_gb300 import _native as N
+
+    lib = N.load()
+    n, k, T, w = 1 << 14, 24, 500, 8
+    half, nb = n // 2, n // (2 * w)
+    a = inputs.complex_normal((T, k), 51)
+    a = (a / np.linalg.norm(a, axis=1, keepdims=True)).astype(np.complex64)
+    beta = torch.from_numpy(inputs.complex_normal((k, half), 52).astype(np.complex64)).cuda()
+    rng = np.random.default_rng(53)
+    cands = np.zeros(3000, dtype=api.CANDIDATE_NP)
+    cands["tmpl"] = rng.integers(0, T, len(cands))
+    cands["bin"] = nb + rng.integers(0, nb, len(cands))
+    cands = np.unique(cands)
+    cd = torch.from_numpy(np.ascontiguousarray(cands).view(np.uint8)).cuda()
+    d = api.make_desc(1024.0, n, k, T, w=w, rho_ii=1.5, cand_capacity=1 << 14)
+    basis = api.Basis(torch.zeros((k, half), dtype=torch.complex64, device="cuda"), torch.from_numpy(a).cuda(), n)
+    api.rb_pack_coeff(d, basis)
+    lib.rbx_set_stage2_tc(1)
+    try:
+        buf, n_ref = api.rb_stage2(d, basis, beta, cd, len(cands), capacity=1 << 14)
+        ref = api.triggers_numpy(buf, n_ref)
+        assert n_ref > 0
+        lib.rbx_stage2_withhold_copies(1)
+        t0 = time.perf_counter()
+        with pytest.raises(N.RBError) as e:
+            api.rb_stage2(d, basis, beta, cd, len(cands), capacity=1 << 14)
+        waited = time.perf_counter() - t0
+        assert e.value.code == N.RB_ERR_TIMEOUT
+        assert b"timed out" in lib.rb_last_error_detail()
+        assert 0.5 < waited < 30.0
+        torch.cuda.synchronize()
+        buf, n2 = api.rb_stage2(d, basis, beta, cd, len(cands), capacity=1 << 14)
+        got = api.triggers_numpy(buf, n2)
+        assert n2 == n_ref
+        for f in ("tmpl", "sample", "snr", "phase"):
+            assert np.array_equal(got[f], ref[f]), f
+    finally:
+        lib.rbx_stage2_withhold_copies(0)
+        lib.rbx_set_stage2_tc(0)
