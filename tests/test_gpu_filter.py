@@ -325,11 +325,12 @@ def test_bucketing_window_and_fallback(api):
 
 
 @pytest.mark.parametrize("w", [1, 2, 4, 8])
-@pytest.mark.parametrize("k", [24, 40, 256])
+@pytest.mark.parametrize("k", [24, 40, 256, 400])
 def test_stage2_tc_parity(api, w, k):
     """The tcgen05 second stage (tiles of 128 candidates, hi and lo windows side by side in one
     N = 32 operand, two products per K step) against the oracle and against the mma.sync second
-    stage on the same candidates, including a hot bin of several tiles."""
+    stage on the same candidates, including a hot bin of several tiles. k = 400 leaves room for a
+    3-stage coefficient ring, k = 256 and below for 5."""
     from paper_2110_13115_gb300 import _native as N
 
     lib = N.load()
