@@ -161,7 +161,7 @@ void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws
       ws->bop_lo = split ? take(plane) : nullptr;
     }
     ws->cand = (rb_candidate*)take(sizeof(rb_candidate) * (size_t)std::max<int64_t>(d.cand_capacity, 1));
-    ws->cand_sorted = (rb_candidate*)take(sizeof(rb_candidate) * (size_t)std::max<int64_t>(d.cand_capacity, 1));
+    ws->cand_sorted = (SortedCand*)take(sizeof(SortedCand) * (size_t)std::max<int64_t>(d.cand_capacity, 1));
     ws->bin_count = (unsigned*)take(sizeof(unsigned) * (size_t)(g.n_bins + 1));
     ws->bin_start = (unsigned*)take(sizeof(unsigned) * (size_t)(g.n_bins + 1));
     // pieces: sum over bins of ceil(c_b / kStage2Piece) <= n_bins + capacity / kStage2Piece

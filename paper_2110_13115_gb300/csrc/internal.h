@@ -31,6 +31,13 @@ struct Tables {
   const float2* fine = nullptr;
 };
 
+// A bucketed candidate: the second stage takes its bin from the work piece, so it keeps only the
+// template row and the block id of the trigger it may become.
+struct alignas(8) SortedCand {
+  int tmpl;
+  int block;
+};
+
 // Carving of the caller's workspace (all offsets 256-byte aligned).
 struct Workspace {
   unsigned* flags = nullptr;                 // RB_FLAG_* bits
@@ -47,7 +54,7 @@ struct Workspace {
   void* bop_hi = nullptr;     // [n_bins][kp] 16-bit
   void* bop_lo = nullptr;     // [n_bins][kp] 16-bit (split precisions)
   rb_candidate* cand = nullptr;
-  rb_candidate* cand_sorted = nullptr;  // candidates grouped by bin for the second stage
+  SortedCand* cand_sorted = nullptr;    // candidates grouped by bin for the second stage
   unsigned* bin_count = nullptr;        // [n_bins + 1] per-bin counts, then fill cursors
   unsigned* bin_start = nullptr;        // [n_bins + 1] exclusive prefix sums
   int4* pieces = nullptr;               // second-stage work items {bin, first, end, 0}

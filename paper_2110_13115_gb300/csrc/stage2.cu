@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const rb_candidate* __restr
                                                      const unsigned long long* dev_count, int64_t cap, int bin0,
                                                      int blo, int nb, const unsigned* __restrict__ start,
                                                      unsigned* __restrict__ cursor,
-                                                     rb_candidate* __restrict__ out) {
+                                                     rb::SortedCand* __restrict__ out) {
   constexpr int PER = 8, CHUNK = 256 * PER;
   __shared__ unsigned hist[kWin];
   __shared__ int red[8];
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const rb_candidate* __restr
       if (b[j] < 0) continue;
       const int d = b[j] - lo;
       const unsigned pos = d < kWin ? hist[d] + r[j] : atomicAdd(cursor + b[j], 1u);
-      out[start[b[j]] + pos] = c[j];
+      out[start[b[j]] + pos] = rb::SortedCand{c[j].tmpl, c[j].block};
     }
     __syncthreads();  // hist and red are reused by the next chunk
   }
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
                                                      const float2* __restrict__ beta, int k, int k16, int T,
                                                      int64_t half, int bin0, const int4* __restrict__ pieces,
                                                      const unsigned* __restrict__ piece_total,
-                                                     const rb_candidate* __restrict__ sorted, float thr2,
+                                                     const rb::SortedCand* __restrict__ sorted, float thr2,
                                                      int64_t sample_offset, rb_trigger* __restrict__ trig,
                                                      unsigned long long* counter, int64_t cap) {
   constexpr int NT = S2<W>::NT;
@@ -431,11 +431,11 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
         if (lane == leader) b0 = atomicAdd(counter, (unsigned long long)__popc(em));
         b0 = __shfl_sync(kFull, b0, leader);
         if (emit) {
-          const rb_candidate cd = sorted[base + g + 8 * h];
+          const rb::SortedCand cd = sorted[base + g + 8 * h];
           const unsigned long long idx = b0 + __popc(em & ((1u << lane) - 1u));
           if ((int64_t)idx < cap) {
             rb_trigger tg;
-            tg.sample = sample_offset + (int64_t)cd.bin * W + br;
+            tg.sample = sample_offset + (int64_t)(bin0 + b) * W + br;
             tg.tmpl = cd.tmpl;
             tg.block = cd.block;
             tg.snr = sqrtf(best);

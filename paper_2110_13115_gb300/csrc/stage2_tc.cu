@@ -59,7 +59,7 @@ struct S2Params {
   int bin0;
   const int4* pieces;
   const unsigned* piece_total;
-  const rb_candidate* sorted;
+  const rb::SortedCand* sorted;
   float thr2;
   int64_t sample_offset;
   rb_trigger* trig;
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
         if (lane == leader) b0c = atomicAdd(p.counter, (unsigned long long)__popc(em));
         b0c = __shfl_sync(kFull, b0c, leader);
         if (emit) {
-          const rb_candidate cd = p.sorted[ci];
+          const rb::SortedCand cd = p.sorted[ci];
           const unsigned long long idx = b0c + __popc(em & ((1u << lane) - 1u));
           if ((int64_t)idx < p.cap) {
             rb_trigger tg;
