@@ -1,8 +1,9 @@
 // Second stage of the hierarchy (arXiv:2110.13115 Sec. III.C, full-resolution reconstruction of
 // every sample inside the triggering bins; Sec. III.E custom kernel), grouped by bin.
 //
-// 1. First-stage candidates are bucketed by bin: per-bin counts (warp-aggregated atomics), an
-//    exclusive scan, and a scatter.
+// 1. First-stage candidates are bucketed by bin: per-bin counts and a scatter, both through
+//    per-chunk shared-memory histograms, around an exclusive scan; the bucketed copy holds
+//    8-byte (template, block) records, the bin coming with the work piece.
 // 2. The scan cuts each non-empty bin into pieces of at most kStage2Piece candidates, so a bin
 //    with thousands of candidates is shared by many CTAs and empty bins cost nothing. For each
 //    piece a CTA stages the bin's k x w window of beta (unless it already holds that bin) as
