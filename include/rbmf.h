@@ -419,6 +419,42 @@ int rb_build(const rb_bank_desc* bank, const double* psd, int32_t k, int32_t ove
              uint64_t seed, float* vectors, float* coeff, double* sigma2, double* sv, void* workspace,
              size_t workspace_bytes, void* stream);
 
+/*
+ * Sub-banks along iso-tau0 lines and the basis size for a tolerance (Sec. III.B, Table I): a large
+ * bank is cut into parts of equal template count in the order of the Newtonian chirp time, each
+ * part gets its own basis (rb_build), and each basis keeps the fewest vectors whose Eq. 8 loss meets
+ * the tolerance. Host only: no device memory, no stream.
+ *
+ * rb_bank_tau0 - tau0[t] = 5 M / (256 eta v^8) with v = (pi M f0)^(1/3), M = m1 + m2 in seconds
+ *   (G M_sun / c^3 = 4.925490947641267e-6 s) and eta = m1 m2 / M^2: the Newtonian chirp time from
+ *   frequency f0 to coalescence, tau0 ~ Mc^(-5/3) f0^(-8/3) (Sec. III.B).
+ *   bank: its params (HOST [T][4]) and n_templates are read.  tau0: [T] float64 HOST output.
+ *   Errors: RB_ERR_BAD_INPUT (NULL pointer, T < 1, f0 not finite and > 0, a mass not > 0).
+ */
+int rb_bank_tau0(const rb_bank_desc* bank, double f0, double* tau0);
+
+/*
+ * rb_bank_split_tau0 - order[] lists the T templates by ascending tau0 (equal values keep their
+ *   index order); part p holds order[offsets[p] .. offsets[p+1]) with offsets[p] = floor(p T / parts),
+ *   so part sizes differ by at most one and every tau0 of part p is <= every tau0 of part p+1.
+ *   tau0: [T] HOST.  order: [T] int64 HOST output.  offsets: [parts + 1] int64 HOST output.
+ *   Errors: RB_ERR_BAD_INPUT (NULL pointer, T < 1, parts < 1 or > T, a tau0 not finite).
+ */
+int rb_bank_split_tau0(const double* tau0, int64_t n_templates, int32_t parts, int64_t* order, int64_t* offsets);
+
+/*
+ * rb_basis_k_for_loss - the fewest basis vectors whose Eq. 8 loss meets `tol`: with rows of unit
+ *   norm the squared singular values of all T rows sum to T, so keeping k' vectors loses
+ *   L(k') = 1 - sum_{j<k'} sv[j]^2 / T, the bank-averaged SNR loss. *k_out = the smallest k' in
+ *   [1, k] with L(k') <= tol, and *loss_out = L(*k_out).
+ *   sv: [k] HOST, descending, from rb_build.  n_templates: T of that rb_build.
+ *   Errors: RB_ERR_BAD_INPUT (NULL pointer, k < 1, T < 1, tol not in [0, 1), sv not descending and
+ *   >= 0, or sum sv^2 > T by more than rounding); RB_ERR_UNSUPPORTED when even L(k) > tol, with
+ *   *k_out = k and *loss_out = L(k) (build a larger basis).
+ */
+int rb_basis_k_for_loss(const double* sv, int32_t k, int64_t n_templates, double tol, int32_t* k_out,
+                        double* loss_out);
+
 /* Candidate refinement (step a8; not in the paper, which stops at the triggers). */
 typedef struct rb_refine_desc {
   double fs;          /* sample rate [Hz] */

@@ -120,6 +120,10 @@ SIGNATURES = {
     "rb_build_plan": (C.c_int, [C.POINTER(rb_bank_desc), C.c_int32, C.c_int32, C.POINTER(C.c_size_t),
                                 C.POINTER(C.c_size_t)]),
     "rb_templates": (C.c_int, [C.POINTER(rb_bank_desc), _P, _P, _P, _P, C.c_size_t, _P]),
+    "rb_bank_tau0": (C.c_int, [C.POINTER(rb_bank_desc), C.c_double, _P]),
+    "rb_bank_split_tau0": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P]),
+    "rb_basis_k_for_loss": (C.c_int, [_P, C.c_int32, C.c_int64, C.c_double, C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_double)]),
     "rb_build": (C.c_int, [C.POINTER(rb_bank_desc), _P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _P, _P, _P,
                            C.POINTER(C.c_double), _P, C.c_size_t, _P]),
 }

@@ -289,6 +289,35 @@ def rb_build_plan(bank: Bank, k: int, oversample: int = 64):
     return t.value, b.value
 
 
+def rb_bank_tau0(bank: Bank, f0: float) -> np.ndarray:
+    """Newtonian chirp time of every template from f0 to coalescence [s] (host)."""
+    out = np.empty(bank.params.shape[0], dtype=np.float64)
+    bd = bank.c_struct()
+    N.check("rb_bank_tau0", _lib().rb_bank_tau0(C.byref(bd), float(f0), out.ctypes.data))
+    return out
+
+
+def rb_bank_split_tau0(tau0: np.ndarray, parts: int):
+    """Templates in ascending tau0 order cut into `parts` equal-count sub-banks: (order, offsets);
+    sub-bank p is order[offsets[p]:offsets[p + 1]] (host)."""
+    tau0 = np.ascontiguousarray(tau0, dtype=np.float64)
+    order = np.empty(len(tau0), dtype=np.int64)
+    offsets = np.empty(int(parts) + 1, dtype=np.int64)
+    N.check("rb_bank_split_tau0", _lib().rb_bank_split_tau0(tau0.ctypes.data, len(tau0), int(parts),
+                                                            order.ctypes.data, offsets.ctypes.data))
+    return order, offsets
+
+
+def rb_basis_k_for_loss(sv: np.ndarray, n_templates: int, tol: float):
+    """Fewest basis vectors whose Eq. 8 loss is <= tol, from rb_build's singular values: (k, loss).
+    Raises RBError(RB_ERR_UNSUPPORTED) when all of sv do not reach tol."""
+    sv = np.ascontiguousarray(sv, dtype=np.float64)
+    k, loss = C.c_int32(0), C.c_double(0.0)
+    N.check("rb_basis_k_for_loss", _lib().rb_basis_k_for_loss(sv.ctypes.data, len(sv), int(n_templates), float(tol),
+                                                              C.byref(k), C.byref(loss)))
+    return k.value, loss.value
+
+
 def rb_templates(bank: Bank, psd: torch.Tensor):
     """Whitened unit-norm templates [T][n/2] complex64 and sigma^2 [T] float64 (device)."""
     tb, _ = rb_build_plan(bank, 1, 0)

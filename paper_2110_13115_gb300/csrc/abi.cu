@@ -795,4 +795,86 @@ int rb_batch_destroy(rb_batch* batch) {
   return rc;
 }
 
+// ---------------------------------------------------------------------------------------
+// Sub-banks along iso-tau0 lines and the basis size for a tolerance (Sec. III.B, Table I). Host only.
+
+int rb_bank_tau0(const rb_bank_desc* bank, double f0, double* tau0) {
+  if (!bank || !bank->params || !tau0 || bank->n_templates < 1) {
+    set_detail("bank, bank->params or tau0 is NULL, or n_templates < 1");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (!(f0 > 0.0) || !std::isfinite(f0)) {
+    set_detail("f0 = %g must be finite and > 0", f0);
+    return RB_ERR_BAD_INPUT;
+  }
+  constexpr double kTsun = 4.925490947641267e-6;  // G M_sun / c^3 [s]
+  constexpr double kPi = 3.14159265358979323846;
+  for (int t = 0; t < bank->n_templates; ++t) {
+    const double m1 = bank->params[4 * t], m2 = bank->params[4 * t + 1];
+    if (!(m1 > 0.0) || !(m2 > 0.0) || !std::isfinite(m1) || !std::isfinite(m2)) {
+      set_detail("template %d: masses (%g, %g) must be finite and > 0", t, m1, m2);
+      return RB_ERR_BAD_INPUT;
+    }
+    const double M = (m1 + m2) * kTsun, eta = m1 * m2 / ((m1 + m2) * (m1 + m2));
+    const double v = std::cbrt(kPi * M * f0), v2 = v * v, v4 = v2 * v2;
+    tau0[t] = 5.0 * M / (256.0 * eta * v4 * v4);
+  }
+  return RB_OK;
+}
+
+int rb_bank_split_tau0(const double* tau0, int64_t n_templates, int32_t parts, int64_t* order, int64_t* offsets) {
+  if (!tau0 || !order || !offsets || n_templates < 1 || parts < 1 || parts > n_templates) {
+    set_detail("NULL pointer, n_templates = %lld < 1 or parts = %d not in [1, n_templates]",
+               (long long)n_templates, parts);
+    return RB_ERR_BAD_INPUT;
+  }
+  for (int64_t t = 0; t < n_templates; ++t) {
+    if (!std::isfinite(tau0[t])) {
+      set_detail("tau0[%lld] is not finite", (long long)t);
+      return RB_ERR_BAD_INPUT;
+    }
+    order[t] = t;
+  }
+  std::stable_sort(order, order + n_templates, [&](int64_t a, int64_t b) { return tau0[a] < tau0[b]; });
+  for (int32_t p = 0; p <= parts; ++p) offsets[p] = (int64_t)((__int128)p * n_templates / parts);
+  return RB_OK;
+}
+
+int rb_basis_k_for_loss(const double* sv, int32_t k, int64_t n_templates, double tol, int32_t* k_out,
+                        double* loss_out) {
+  if (!sv || !k_out || !loss_out || k < 1 || n_templates < 1 || !(tol >= 0.0 && tol < 1.0)) {
+    set_detail("NULL pointer, k = %d < 1, n_templates = %lld < 1 or tol = %g not in [0, 1)", k,
+               (long long)n_templates, tol);
+    return RB_ERR_BAD_INPUT;
+  }
+  const double T = (double)n_templates;
+  double kept = 0.0;
+  for (int32_t j = 0; j < k; ++j) {
+    if (!(sv[j] >= 0.0) || !std::isfinite(sv[j]) || (j > 0 && sv[j] > sv[j - 1])) {
+      set_detail("sv[%d] = %g: singular values must be finite, >= 0 and descending", j, sv[j]);
+      return RB_ERR_BAD_INPUT;
+    }
+    kept += sv[j] * sv[j];
+  }
+  if (kept > T * (1.0 + 1e-6)) {
+    set_detail("sum of sv^2 = %.17g exceeds n_templates = %lld: rows are not unit-normalised", kept,
+               (long long)n_templates);
+    return RB_ERR_BAD_INPUT;
+  }
+  kept = 0.0;
+  for (int32_t j = 0; j < k; ++j) {
+    kept += sv[j] * sv[j];
+    const double loss = std::max(0.0, 1.0 - kept / T);
+    if (loss <= tol) {
+      *k_out = j + 1;
+      *loss_out = loss;
+      return RB_OK;
+    }
+  }
+  *k_out = k;
+  *loss_out = std::max(0.0, 1.0 - kept / T);
+  set_detail("the %d singular values leave an Eq. 8 loss of %.3g > tol = %.3g", k, *loss_out, tol);
+  return RB_ERR_UNSUPPORTED;
+}
+
 }  // extern "C"
