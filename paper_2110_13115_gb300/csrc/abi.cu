@@ -836,7 +836,9 @@ int rb_bank_split_tau0(const double* tau0, int64_t n_templates, int32_t parts, i
     order[t] = t;
   }
   std::stable_sort(order, order + n_templates, [&](int64_t a, int64_t b) { return tau0[a] < tau0[b]; });
-  for (int32_t p = 0; p <= parts; ++p) offsets[p] = (int64_t)((__int128)p * n_templates / parts);
+  // floor(p T / parts) = p q + floor(p r / parts) with T = q parts + r: no intermediate overflows
+  const int64_t q = n_templates / parts, r = n_templates % parts;
+  for (int32_t p = 0; p <= parts; ++p) offsets[p] = (int64_t)p * q + ((int64_t)p * r) / parts;
   return RB_OK;
 }
 
