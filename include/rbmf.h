@@ -145,6 +145,8 @@ int rb_whiten(const rb_filter_desc* desc, const float* strain, const double* psd
  *   s_hat: [n/2] complex (rb_whiten output).  basis->vectors: [k][n/2] complex.
  *   beta: [k][n/2] complex output (index m - n/2), may be NULL to skip storing it.
  *   beta_avg: [k][n/(2w)] complex output (index i - n/(2w)).
+ *   Errors: RB_ERR_BAD_INPUT (desc invalid, basis not matching desc, NULL s_hat or beta_avg),
+ *   RB_ERR_OOM (workspace smaller than rb_filter_plan's size or not 256-byte aligned).
  */
 int rb_basis_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* s_hat,
                     float* beta, float* beta_avg, void* workspace, size_t workspace_bytes,
@@ -221,6 +223,8 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
  * so no SNR series reaches memory.
  *   templates: [T][n/2] complex whitened unit-norm templates (g_t / sigma_t).
  *   strain, psd, trig, capacity, n_trig: as rb_filter (desc->k, w, rho_ii used; rho_i ignored).
+ *   Errors: RB_ERR_BAD_INPUT (NULL array, negative capacity, PSD not finite and > 0 on 0 < j < n/2),
+ *   RB_ERR_OOM (workspace), RB_ERR_OVERFLOW (more triggers than capacity; *n_trig = the count).
  */
 int rb_filter_plain(const rb_filter_desc* desc, const float* templates, const float* strain,
                     const double* psd, rb_trigger* trig, int64_t capacity, int64_t* n_trig,
@@ -319,6 +323,8 @@ int rb_batch_destroy(rb_batch* batch);
  * when untuned). Measurement support, not in the paper.
  *   beta_avg: [k][n/(2w)] complex device.  times_ms: HOST [RB_STAGE1_VARIANTS] mean ms per launch.
  *   chosen: HOST, the selected variant. Synchronises `stream`.
+ *   Errors: RB_ERR_BAD_INPUT (NULL argument, basis not matching desc, an FP32 desc or a coeff_op not
+ *   packed for desc's precision), RB_ERR_OOM (workspace), RB_ERR_TIMEOUT (a variant's bounded wait).
  */
 #define RB_STAGE1_VARIANTS 2
 /* rb_set_stage1_variant - pin the tile variant (0: N-tile 256, 1: N-tile 128) used for desc's shape
@@ -335,6 +341,7 @@ int rb_tune_stage1(const rb_filter_desc* desc, const rb_basis* basis, const floa
  * table (variant 0 when untuned). Measurement support, not in the paper.
  *   s_hat: [n/2] complex device (rb_whiten output). times_ms: HOST [RB_FFT_VARIANTS] mean ms of one
  *   basis filter. chosen: HOST, the selected variant. Synchronises `stream`.
+ *   Errors: RB_ERR_BAD_INPUT (NULL argument, basis not matching desc), RB_ERR_OOM (workspace).
  */
 #define RB_FFT_VARIANTS 8
 int rb_tune_fft(const rb_filter_desc* desc, const rb_basis* basis, const float* s_hat, double* times_ms,
@@ -389,12 +396,14 @@ int rb_build_plan(const rb_bank_desc* bank, int32_t k, int32_t oversample, size_
                   size_t* build_bytes /* host */);
 
 /*
- * rb_templates - whitened, unit-normalised templates g_t / sigma_t on j in [0, n/2) (rows of the
- * template matrix of Sec. III.B: "whitened ... and normalized to unity"), with
+ * rb_templates - whitened, unit-normalised templates g_t / sigma_t on j in [0, n/2) (the rows of the
+ * template matrix of Sec. III.B, each whitened by the PSD and scaled to norm one), with
  * g_t[j] = sqrt(4 df / S_j) h_t(f_j) and sigma_t^2 = sum_j |g_t[j]|^2 = <h_t|h_t> (Eq. 2) in FP64.
  * The phase is evaluated in FP64, reduced modulo 2 pi, then sin/cos in FP32.
  *   psd: [n/2+1] float64 device.  out: [T][n/2] complex device.  sigma2: [T] float64 device.
  *   workspace: templates_bytes of rb_build_plan. Enqueue only.
+ *   Errors: RB_ERR_BAD_INPUT (NULL array, bank sizes or pn_order), RB_ERR_OOM (workspace smaller than
+ *   templates_bytes).
  */
 int rb_templates(const rb_bank_desc* bank, const double* psd, float* out, double* sigma2, void* workspace,
                  size_t workspace_bytes, void* stream);
@@ -480,13 +489,15 @@ typedef struct rb_refine_desc {
  */
 size_t rb_refine_workspace_bytes(const rb_refine_desc* desc);
 
-/* rb_refine_eval - J [n_cand] and Z [n_cand] complex (float64 pairs) at theta (the forward pass). */
+/* rb_refine_eval - J [n_cand] and Z [n_cand] complex (float64 pairs) at theta (the forward pass).
+ * Errors: RB_ERR_BAD_INPUT (NULL output, sizes, PSD not finite and > 0 on 0 < j < n/2, a candidate with
+ * mc <= 0, eta outside (0, 0.25] or non-finite t_c / phi_c), RB_ERR_OOM (workspace). */
 int rb_refine_eval(const rb_refine_desc* desc, const float* s_hat, const double* psd, const double* theta,
                    double* J, double* Z, int64_t n_cand, void* workspace, size_t workspace_bytes, void* stream);
 
 /* rb_refine_adjoint - the backward pass: given dL/dJ [n_cand] and the forward Z, recomputes the
  * templates and returns dL/dtheta [n_cand][4] = dL/dJ * 2 Re(conj(Z) dZ/dtheta) / sigma^2 with
- * dZ/dtheta = sum_j s_hat[j] (i dPsi_j/dtheta) conj(g_j). */
+ * dZ/dtheta = sum_j s_hat[j] (i dPsi_j/dtheta) conj(g_j). Errors: as rb_refine_eval. */
 int rb_refine_adjoint(const rb_refine_desc* desc, const float* s_hat, const double* psd, const double* theta,
                       const double* Z, const double* dJ, double* dtheta, int64_t n_cand, void* workspace,
                       size_t workspace_bytes, void* stream);

@@ -1,10 +1,11 @@
-// First-stage reconstruction on tcgen05 tensor cores (arXiv:2110.13115 Sec. III.C first stage,
-// Sec. III.E "multiplying beta^avg and D"): z_avg[t, i] = sum_k conj(a_tk) beta_avg_k[i] as one
-// real contraction over K = 2k,
+// First-stage reconstruction on tcgen05 tensor cores (arXiv:2110.13115 Sec. III.C first stage; the
+// product of the bin-averaged basis series with the coefficient matrix of Sec. III.E):
+// z_avg[t, i] = sum_k conj(a_tk) beta_avg_k[i] as one real contraction over K = 2k,
 //   rows 2t   [Re a_t, Im a_t]   . [Re b_i, Im b_i] = Re z_avg[t, i]
 //   rows 2t+1 [-Im a_t, Re a_t]  . [Re b_i, Im b_i] = Im z_avg[t, i],
-// with 16-bit operands (one plane, or hi + lo planes with three products hi.hi + hi.lo + lo.hi)
-// and FP32 accumulators in tensor memory. The epilogue squares, pairs the Re/Im rows across
+// with 16-bit operands (one plane each; hi + lo planes of both with three products hi.hi + hi.lo +
+// lo.hi; or hi + lo planes of A against one plane of B with two products) and FP32 accumulators in
+// tensor memory. The epilogue squares, pairs the Re/Im rows across
 // neighbouring lanes, tests |z_avg|^2 >= rho_I^2 and appends candidates; the T x bins array
 // never reaches global memory.
 //
