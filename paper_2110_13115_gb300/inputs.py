@@ -6,9 +6,9 @@ matched-filter arithmetic (no whitening, no filtering, no basis, no
 thresholds); the CUDA path and the CPU oracle both consume what it returns.
 
 The paper filters PyCBC-generated coloured Gaussian noise against an O2
-template bank (Sec. IV, "Comparing Performance with Template Based Matched
-Filtering").  Neither is available here, so the synthetic workloads below
-stand in for them:
+template bank (Sec. IV, its comparison with the template-by-template matched
+filter).  Neither is available here, so the synthetic workloads below stand in
+for them:
 
 * noise: stationary Gaussian noise coloured by the analytic one-sided PSD
   ``S(f) = A [(f/40)^-4 + 2 + 2 (f/40)^2]`` with ``A = 1`` (internal units),
