@@ -2,8 +2,10 @@
 // static device array instead of a caller-provided workspace, for callers that cannot allocate
 // device memory. The array is part of the library's device image, so every GPU that loads the
 // library holds RB_STATIC_SCRATCH_BYTES of it until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
 
 #include "common.cuh"
@@ -13,9 +15,60 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_static_scratch[RB_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
+// The host-side name of the array is a stand-in, not a device address: the device address is
+// asked of the runtime (cudaGetSymbolAddress) with the device current. It belongs to the CUDA
+// context that loaded the module, so it is kept per context id (unique for the life of the
+// process): after cudaDeviceReset the device gets a new primary context, the module is loaded
+// again, possibly elsewhere, and the next call looks the address up afresh.
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
 std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};  // device address of g_static_scratch, per device
+std::map<unsigned long long, void*> g_scratch_by_ctx;
+
+template <class F>
+F driver_entry(const char* name) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<F>(p);
+}
+
+// Id of the calling thread's current context; false when there is none yet or the driver lacks
+// the query.
+bool current_ctx_id(unsigned long long* id) {
+  static const PfnCtxGetCurrent get_current = driver_entry<PfnCtxGetCurrent>("cuCtxGetCurrent");
+  static const PfnCtxGetId get_id = driver_entry<PfnCtxGetId>("cuCtxGetId");
+  if (!get_current || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+int scratch_address(void** out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  unsigned long long id = 0;
+  if (current_ctx_id(&id)) {
+    auto it = g_scratch_by_ctx.find(id);
+    if (it != g_scratch_by_ctx.end()) {
+      *out = it->second;
+      return RB_OK;
+    }
+  }
+  // set-up, once per context: this query also binds the device's primary context if the thread
+  // had none, so the id is read again afterwards
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    rb::set_detail("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+    return RB_ERR_CUDA;
+  }
+  if (current_ctx_id(&id)) g_scratch_by_ctx[id] = p;
+  *out = p;
+  return RB_OK;
+}
 
 }  // namespace
 
@@ -31,23 +84,7 @@ extern "C" int rb_filter_static(const rb_filter_desc* desc, const rb_basis* basi
                    sizes.workspace_bytes, (size_t)RB_STATIC_SCRATCH_BYTES);
     return RB_ERR_UNSUPPORTED;
   }
-  int dev = 0;
-  RB_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    rb::set_detail("device ordinal %d out of range", dev);
-    return RB_ERR_UNSUPPORTED;
-  }
   void* scratch = nullptr;
-  {
-    // one-time set-up per device, with that device current: the host-side name of the array is
-    // not a device address, so ask the runtime for the device address once and keep it
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      RB_CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
-      g_scratch_addr[dev] = p;
-    }
-    scratch = g_scratch_addr[dev];
-  }
+  if ((rc = scratch_address(&scratch))) return rc;
   return rb_filter(desc, basis, strain, psd, trig, capacity, n_trig, scratch, (size_t)RB_STATIC_SCRATCH_BYTES, stream);
 }

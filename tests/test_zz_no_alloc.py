@@ -26,10 +26,10 @@ def api():
     return A
 
 
-def _static_call(api, d, basis, strain, psd, cap):
+def _static_call(api, d, basis, strain, psd, cap, trig=None):
     from paper_2110_13115_gb300 import _native as N
 
-    trig = torch.empty(cap * 24, dtype=torch.uint8, device="cuda")
+    trig = torch.empty(cap * 24, dtype=torch.uint8, device="cuda") if trig is None else trig
     n = C.c_int64(0)
     b = basis.c_struct()
     rc = N.load().rb_filter_static(C.byref(d), C.byref(b), C.c_void_p(strain.data_ptr()), C.c_void_p(psd.data_ptr()),
@@ -56,9 +56,18 @@ def test_static_scratch_matches_workspace_path(api, prec):
     ref_buf, n_ref = api.rb_filter(d, basis, strain, psd, capacity=cap)
     ref = api.triggers_numpy(ref_buf, n_ref)
     assert n_ref > 0
-    for _ in range(2):  # two calls in a row: the shared array keeps no state that matters
-        rc, buf, n = _static_call(api, d, basis, strain, psd, cap)
+    trig = torch.empty(cap * 24, dtype=torch.uint8, device="cuda")
+    for call in range(2):  # two calls in a row: the shared array keeps no state that matters
+        torch.cuda.synchronize()
+        alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+        free0, total = torch.cuda.mem_get_info()
+        rc, buf, n = _static_call(api, d, basis, strain, psd, cap, trig=trig)
+        torch.cuda.synchronize()
         assert rc == N.RB_OK, N.load().rb_last_error_detail()
+        if call == 1:  # the call itself allocates nothing (the first may still grow driver-side pools)
+            assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == reserved0
+            free1, _ = torch.cuda.mem_get_info()
+            assert free0 - free1 <= (2 << 20), (free0, free1)
         got = api.triggers_numpy(buf, n)
         assert n == n_ref
         assert np.array_equal(got["tmpl"], ref["tmpl"]) and np.array_equal(got["sample"], ref["sample"])
