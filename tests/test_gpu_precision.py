@@ -27,7 +27,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 PRECISIONS = ["fp32", "fp16_split", "bf16_split", "fp16_split_a", "fp16", "bf16"]
 # the 1e-4 tolerance on the FP32 SNR holds for the FP32 and split paths; the plain 16-bit
 # paths are reported (about 2^-9 and 2^-12 relative per operand), with a loose sanity bound
-BOUND = {"fp32": 1e-5, "fp16_split": 1e-4, "bf16_split": 1e-4, "fp16_split_a": 2e-3, "fp16": 2e-2, "bf16": 5e-2}
+BOUND = {"fp32": 1e-5, "fp16_split": 1e-4, "bf16_split": 1e-4, "fp16_split_a": 1e-3, "fp16": 2e-2, "bf16": 5e-2}
 SAMPLE = 200_000  # candidates compared per precision (all of them when fewer; top SNRs always)
 
 

@@ -12,8 +12,16 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # worst relative error of |z_avg| expected per precision (hi+lo splits keep ~16-22 bits; splitting only
-# the coefficients leaves beta_avg's FP16 rounding, about 2^-11 per element)
-REL = {"fp16_split": 2e-5, "bf16_split": 1e-4, "fp16": 3e-3, "bf16": 2e-2, "fp16_split_a": 2e-3}
+# the coefficients leaves beta_avg's FP16 rounding, about 2^-11 per element, which stays below the
+# 1e-3 relative SNR tolerance of the screen)
+REL = {"fp16_split": 2e-5, "bf16_split": 1e-4, "fp16": 3e-3, "bf16": 2e-2, "fp16_split_a": 1e-3}
+# modes whose screening decisions must agree with the oracle outside a 1e-3 band around rho_I; the
+# plain 16-bit modes are reported with a band of twice their own error
+SPLIT = ("fp16_split", "bf16_split", "fp16_split_a")
+
+
+def _band(prec):
+    return 1e-3 if prec in SPLIT else max(REL[prec] * 2, 1e-3)
 
 
 @pytest.fixture(scope="module")
@@ -52,7 +60,7 @@ def _case(api, T, k, n, w, rho_i, prec, seed=1, variant=0):
 def test_stage1_tc_parity(api, prec, T, k, n, w, variant):
     rho_i = 2.6
     got, ref, r, nb = _case(api, T, k, n, w, rho_i, prec, variant=variant)
-    band = max(REL[prec] * 2, 1e-3)
+    band = _band(prec)
     gset = set(zip(got["tmpl"].tolist(), got["bin"].tolist()))
     oset = set(zip(ref["template"].tolist(), ref["bin"].tolist()))
     assert len(oset) > 20
@@ -113,7 +121,7 @@ def test_pipeline_tc_real_bank_vs_oracle_rb(api, prec, w, rho_i):
     half = g.n // 2
     zfull = np.abs(rb.reconstruct(a, beta[:, half:]))
     ravg = np.abs(rb.reconstruct(a, rb.bin_average(beta, w)[:, g.n // (2 * w):]))
-    band = max(2 * REL[prec], 1e-3)
+    band = _band(prec)
     stats = compare_triggers(got, ref, w, rho_ii, ref_rho=zfull, rho_avg=ravg, rho_i=rho_i, band=band)
     assert stats["both"] >= 3, stats
 
