@@ -14,7 +14,8 @@
  *  - Whitened coordinates: x_hat[j] = sqrt(4 df / S_j) x(f_j), with x(f) = dt * DFT(x).
  *    In them the inner product <a|b> of Eq. (1) is sum_j a_hat[j] conj(b_hat[j]).
  *  - Complex arrays are interleaved float pairs (re, im), C order as stated per argument.
- *  - Pointers are DEVICE pointers unless the argument says "host". All buffers are owned
+ *  - Pointers are DEVICE pointers unless the argument says "host", or unless rb_filter_desc.mem
+ *    tags them as host pointers (rb_filter and rb_filter_static only, see RB_MEM_*). All buffers are owned
  *    by the caller; the library allocates no device memory (beyond the CUDA graph objects that
  *    rb_batch_create records): every call that needs scratch space takes a caller-provided
  *    workspace of at least the size rb_filter_plan reports (256-byte aligned).
@@ -54,6 +55,16 @@ enum {
   RB_PREC_FP16_SPLIT_A = 5 /* tcgen05 FP16, coefficients split hi+lo, beta_avg single: 2 MMAs */
 };
 
+/* Where rb_filter's strain and trigger buffers live (rb_filter_desc.mem bits; 0 = both on the
+ * device). With a host bit set, rb_filter copies through device staging inside its workspace on the
+ * caller's stream: the strain in before the whitening FFT, the triggers out after the second stage
+ * (the call already synchronises the stream to return the count). Host buffers may be pageable;
+ * pinned ones let the copies run at full link speed. */
+enum {
+  RB_MEM_HOST_STRAIN = 1,   /* strain is a host pointer ([n] float32) */
+  RB_MEM_HOST_TRIGGERS = 2  /* trig is a host pointer; capacity <= rb_filter_sizes.host_trig_capacity */
+};
+
 /* One block's filtering parameters. */
 typedef struct rb_filter_desc {
   double fs;              /* sample rate [Hz] */
@@ -67,7 +78,7 @@ typedef struct rb_filter_desc {
   int64_t cand_capacity;  /* first-stage candidate slots kept in the workspace, < 2^31 */
   int64_t sample_offset;  /* global index of block sample 0 */
   int32_t block_id;       /* copied into rb_trigger.block / rb_candidate.block */
-  int32_t reserved;       /* must be 0 */
+  int32_t mem;            /* RB_MEM_* bits (rb_filter, rb_filter_static); 0 for every other call */
 } rb_filter_desc;
 
 /* The reduced basis of a template bank (output of rb_build; caller-owned arrays). */
@@ -106,6 +117,8 @@ typedef struct rb_filter_sizes {
   int32_t n1, n2;           /* four-step split n = n1 * n2 */
   int32_t kp;               /* stage-1 contraction length 2k rounded up to 64 */
   size_t coeff_op_bytes;    /* bytes rb_pack_coeff writes for desc->precision */
+  int64_t host_trig_capacity; /* largest rb_filter capacity with RB_MEM_HOST_TRIGGERS (staging in the
+                                 workspace's four-step intermediate, free during the second stage) */
 } rb_filter_sizes;
 
 /* Name of a status code (static string). */
@@ -118,7 +131,7 @@ int rb_version(void);
 /*
  * rb_filter_plan - validate `desc` and report workspace size and layout parameters.
  * Host only. Errors: RB_ERR_BAD_INPUT (n not a power of two in range, k < 1, T < 1,
- * w not in {1,2,4,8,16}, w > n/2, thresholds negative or NaN, reserved != 0),
+ * w not in {1,2,4,8,16}, w > n/2, thresholds negative or NaN, mem with bits other than RB_MEM_*),
  * RB_ERR_UNSUPPORTED (precision unknown).
  */
 int rb_filter_plan(const rb_filter_desc* desc, rb_filter_sizes* out /* host */);
@@ -207,13 +220,46 @@ int rb_stage2(const rb_filter_desc* desc, const rb_basis* basis, const float* be
  * rb_filter - the whole hierarchical filter of one block: a1 (rb_whiten), a2+a3
  * (rb_basis_filter), a4 (rb_stage1), a5 (rb_stage2), all on `stream`, beta kept in the
  * workspace. Paper: Sec. III.C (the six bullets) and Sec. III.E.
- *   strain: [n] float32. psd: [n/2+1] float64.  trig: [capacity]; n_trig (host).
+ *   strain: [n] float32 (host when desc->mem has RB_MEM_HOST_STRAIN). psd: [n/2+1] float64.
+ *   trig: [capacity] (host when desc->mem has RB_MEM_HOST_TRIGGERS); n_trig (host).
+ *   With host buffers the copies run on `stream` inside the call, so one call takes strain in
+ *   host memory to triggers in host memory.
  *   Errors: as the stage calls; RB_ERR_OVERFLOW from either stage sets *n_trig to the
- *   required trigger count when known, else to -1 (candidate list overflowed).
+ *   required trigger count when known, else to -1 (candidate list overflowed); RB_ERR_BAD_INPUT
+ *   when capacity exceeds host_trig_capacity with RB_MEM_HOST_TRIGGERS.
  */
 int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* strain,
               const double* psd, rb_trigger* trig, int64_t capacity, int64_t* n_trig,
               void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rb_banks_plan - workspace for rb_filter_banks: the largest rb_filter_plan workspace over the sub-bank
+ * descriptors (they share one workspace in turn). n_bins, n1 and n2 as rb_filter_plan (equal for all),
+ * kp the largest, coeff_op_bytes 0 (pack each sub-bank with rb_pack_coeff and its own desc),
+ * host_trig_capacity the smallest. Host only.
+ * Errors: as rb_filter_plan for any desc; RB_ERR_BAD_INPUT when n_banks < 1 or a desc differs from
+ * descs[0] in n, fs, w or mem.
+ */
+int rb_banks_plan(const rb_filter_desc* descs, int32_t n_banks, rb_filter_sizes* out /* host */);
+
+/*
+ * rb_filter_banks - one block through the hierarchical filter of a bank cut into sub-banks, each with
+ * its own reduced basis: the paper splits its bank along lines of equal chirp time tau0 and gives
+ * every part the basis size that its tolerance needs (Sec. III.B, Table I). The strain is whitened
+ * once (a1); then for every sub-bank b in order the basis filter (a2 + a3), the first stage (a4) and
+ * the second stage (a5) run with descs[b] and bases[b], all appending to one trigger list on `stream`.
+ * A trigger's tmpl is its row in the concatenation of the sub-banks' coefficient matrices:
+ * sum_{b' < b} descs[b'].n_templates + the row in bases[b].
+ *   descs: [n_banks] HOST; same fs, n, w and mem (k, T, precision, rho_i, rho_ii, cand_capacity may
+ *     differ); sample_offset and block_id are taken from descs[0]; mem tags strain / trig as host
+ *     buffers as for rb_filter.
+ *   bases: [n_banks] HOST array; bases[b] matches descs[b] and is packed by rb_pack_coeff for it.
+ *   strain, psd, trig, capacity, n_trig: as rb_filter.   workspace: rb_banks_plan size.
+ *   Errors: as rb_filter; a sub-bank's candidate overflow sets *n_trig = -1 (RB_ERR_OVERFLOW).
+ */
+int rb_filter_banks(const rb_filter_desc* descs, const rb_basis* bases, int32_t n_banks, const float* strain,
+                    const double* psd, rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* workspace,
+                    size_t workspace_bytes, void* stream);
 
 /*
  * rb_filter_plain - the template method (Sec. II, Eq. 4; the baseline of Sec. IV.B.2):
@@ -243,8 +289,10 @@ int rb_filter_plain(const rb_filter_desc* desc, const float* templates, const fl
  * that size are rejected with RB_ERR_UNSUPPORTED (e.g. n = 16384, k = 64, T = 64 fits; the
  * 2^19-sample, k = 256 workload does not). The call itself allocates nothing (no cudaMalloc, no
  * allocating library routine).
- *   - The first call on each device looks up the array's device address (once per device, with
- *     that device current); make that first call before any stream capture.
+ *   - The first call in each CUDA context of a device looks up the array's device address, with
+ *     that device current, and keeps it for that context; make that first call before any stream
+ *     capture. After cudaDeviceReset the device has a new context, where the module may load at
+ *     another address, so the next call is a first call again.
  *   - All calls share the one array and it keeps the last call's contents (every value a call
  *     reads is written or cleared by that call first). Calls that overlap on the GPU - from two
  *     streams or two host threads at once - race on it: serialise them.
@@ -463,6 +511,19 @@ int rb_bank_split_tau0(const double* tau0, int64_t n_templates, int32_t parts, i
  */
 int rb_basis_k_for_loss(const double* sv, int32_t k, int64_t n_templates, double tol, int32_t* k_out,
                         double* loss_out);
+
+/*
+ * rb_basis_max_loss - the worst single-template SNR loss of every basis size: for q in [0, k),
+ *   loss[q] = max_t (1 - sum_{j<=q} |a_tj|^2), the relative SNR that template t loses, against the
+ *   template method, on its own noiseless signal when only the first q + 1 basis vectors are kept
+ *   (rows of unit norm, residual orthogonal to the span: rho_k / rho = 1 - r_t^2, the per-template
+ *   quantity that Eq. 8 averages over the bank, Sec. III.B). Sums in FP64; values clamped at 0.
+ *   basis->coeff: [T][k] device (rb_build output, rows in SNR units).  loss: [k] float64 HOST output.
+ *   workspace: >= 8 k device bytes, 256-byte aligned. Synchronises `stream`.
+ *   Errors: RB_ERR_BAD_INPUT (NULL pointer, k or T < 1), RB_ERR_OOM (workspace), RB_ERR_UNSUPPORTED
+ *   (k > 6144).
+ */
+int rb_basis_max_loss(const rb_basis* basis, double* loss, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Candidate refinement (step a8; not in the paper, which stops at the triggers). */
 typedef struct rb_refine_desc {

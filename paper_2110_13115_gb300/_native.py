@@ -30,6 +30,9 @@ RB_PREC_BF16_SPLIT = 2
 RB_PREC_FP16 = 3
 RB_PREC_BF16 = 4
 RB_PREC_FP16_SPLIT_A = 5
+RB_MEM_HOST_STRAIN = 1
+RB_MEM_HOST_TRIGGERS = 2
+
 PRECISIONS = {"fp32": 0, "fp16_split": 1, "bf16_split": 2, "fp16": 3, "bf16": 4, "fp16_split_a": 5}
 
 
@@ -37,7 +40,7 @@ class rb_filter_desc(C.Structure):
     _fields_ = [("fs", C.c_double), ("n", C.c_int64), ("k", C.c_int32), ("n_templates", C.c_int32),
                 ("w", C.c_int32), ("precision", C.c_int32), ("rho_i", C.c_float), ("rho_ii", C.c_float),
                 ("cand_capacity", C.c_int64), ("sample_offset", C.c_int64), ("block_id", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("mem", C.c_int32)]
 
 
 class rb_basis(C.Structure):
@@ -57,7 +60,7 @@ class rb_candidate(C.Structure):
 
 class rb_filter_sizes(C.Structure):
     _fields_ = [("workspace_bytes", C.c_size_t), ("n_bins", C.c_int64), ("n1", C.c_int32), ("n2", C.c_int32),
-                ("kp", C.c_int32), ("coeff_op_bytes", C.c_size_t)]
+                ("kp", C.c_int32), ("coeff_op_bytes", C.c_size_t), ("host_trig_capacity", C.c_int64)]
 
 
 class rb_bank_desc(C.Structure):
@@ -98,6 +101,9 @@ SIGNATURES = {
     "rb_filter": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_plain": (C.c_int, [_D, _P, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_static": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P]),
+    "rb_banks_plan": (C.c_int, [_D, C.c_int32, C.POINTER(rb_filter_sizes)]),
+    "rb_filter_banks": (C.c_int, [_D, _B, C.c_int32, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
+    "rb_basis_max_loss": (C.c_int, [_B, C.POINTER(C.c_double), _P, C.c_size_t, _P]),
     "rb_batch_plan": (C.c_int, [_D, C.c_int32, C.POINTER(C.c_size_t)]),
     "rb_filter_batch": (C.c_int, [_D, _B, C.c_int32, C.POINTER(rb_block), C.c_int64, _P, C.c_int64, _I64P, _P,
                                   C.c_size_t, _P]),

@@ -31,10 +31,10 @@ def _lib():
 
 
 def make_desc(fs, n, k, n_templates, w=8, precision="fp32", rho_i=0.0, rho_ii=5.0, cand_capacity=1 << 20,
-              sample_offset=0, block_id=0) -> N.rb_filter_desc:
+              sample_offset=0, block_id=0, mem=0) -> N.rb_filter_desc:
     prec = N.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return N.rb_filter_desc(float(fs), int(n), int(k), int(n_templates), int(w), prec, float(rho_i), float(rho_ii),
-                            int(cand_capacity), int(sample_offset), int(block_id), 0)
+                            int(cand_capacity), int(sample_offset), int(block_id), int(mem))
 
 
 def rb_filter_plan(desc) -> N.rb_filter_sizes:
@@ -147,6 +147,84 @@ def rb_filter(desc, basis: Basis, strain: torch.Tensor, psd: torch.Tensor, capac
                           _p(ws), ws.numel(), _stream())
     N.check("rb_filter", rc)
     return trig, n.value
+
+
+def _host_ptr(x):
+    """Address of a host buffer: a C-contiguous numpy array or a contiguous CPU torch tensor."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return C.c_void_p(x.ctypes.data)
+    assert x.device.type == "cpu" and x.is_contiguous()
+    return C.c_void_p(x.data_ptr())
+
+
+def rb_filter_host(desc, basis: Basis, strain, psd: torch.Tensor, trig, capacity=None, ws=None) -> int:
+    """rb_filter with the strain and the triggers in host memory (desc.mem gets both RB_MEM_* bits):
+    the library copies the strain in and the triggers out on the current stream inside the one call.
+    strain: float32 [n] host buffer; trig: host buffer of `capacity` records (TRIGGER_NP numpy array
+    or a uint8 CPU tensor of capacity * 24 bytes). Returns the trigger count."""
+    ws = workspace(desc) if ws is None else ws
+    if capacity is None:
+        capacity = len(trig) if isinstance(trig, np.ndarray) and trig.dtype == TRIGGER_NP else trig.numel() // 24
+    d = N.rb_filter_desc.from_buffer_copy(desc)
+    d.mem = N.RB_MEM_HOST_STRAIN | N.RB_MEM_HOST_TRIGGERS
+    n = C.c_int64(0)
+    b = basis.c_struct()
+    rc = _lib().rb_filter(C.byref(d), C.byref(b), _host_ptr(strain), _p(psd), _host_ptr(trig), int(capacity),
+                          C.byref(n), _p(ws), ws.numel(), _stream())
+    N.check("rb_filter", rc)
+    return n.value
+
+
+# --- sub-banks --------------------------------------------------------------------------------
+
+def rb_banks_plan(descs) -> N.rb_filter_sizes:
+    d = (N.rb_filter_desc * len(descs))(*descs)
+    out = N.rb_filter_sizes()
+    N.check("rb_banks_plan", _lib().rb_banks_plan(d, len(descs), C.byref(out)))
+    return out
+
+
+def banks_workspace(descs, device="cuda") -> torch.Tensor:
+    return torch.empty(rb_banks_plan(descs).workspace_bytes, dtype=torch.uint8, device=device)
+
+
+def rb_filter_banks(descs, bases, strain, psd: torch.Tensor, capacity=1 << 22, ws=None, trig=None, host=False):
+    """One block through every sub-bank (whitened once); returns (trigger buffer, count). Template rows
+    of the triggers index the concatenation of the sub-banks. With host=True, `strain` and `trig` are
+    host buffers (numpy or CPU tensors) and the library copies them on the current stream."""
+    ws = banks_workspace(descs) if ws is None else ws
+    descs = [N.rb_filter_desc.from_buffer_copy(d) for d in descs]
+    for d in descs:
+        d.mem = (N.RB_MEM_HOST_STRAIN | N.RB_MEM_HOST_TRIGGERS) if host else 0
+    if trig is None:
+        trig = (np.zeros(capacity, dtype=TRIGGER_NP) if host else
+                torch.empty(max(capacity, 1) * 24, dtype=torch.uint8, device=ws.device))
+    d, b = _pairs(descs, bases)
+    n = C.c_int64(0)
+    sp = _host_ptr(strain) if host else _p(strain)
+    tp = _host_ptr(trig) if host else _p(trig)
+    rc = _lib().rb_filter_banks(d, b, len(descs), sp, _p(psd), tp, int(capacity), C.byref(n), _p(ws), ws.numel(),
+                                _stream())
+    N.check("rb_filter_banks", rc)
+    return trig, n.value
+
+
+def rb_basis_max_loss(basis: Basis) -> np.ndarray:
+    """Worst single-template truncation loss for every basis size 1..k (float64 [k], host)."""
+    ws = torch.empty(max(8 * basis.k, 256), dtype=torch.uint8, device=basis.coeff.device)
+    out = np.zeros(basis.k, dtype=np.float64)
+    b = basis.c_struct()
+    N.check("rb_basis_max_loss", _lib().rb_basis_max_loss(C.byref(b), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                                          _p(ws), ws.numel(), _stream()))
+    return out
+
+
+def truncate(basis: Basis, k: int) -> Basis:
+    """The first k vectors of a basis (vectors are ordered by singular value) and their coefficients."""
+    sv = None if basis.singular_values is None else basis.singular_values[:k]
+    return Basis(basis.vectors[:k].contiguous(), basis.coeff[:, :k].contiguous(), basis.n, sigma2=basis.sigma2,
+                 singular_values=sv)
 
 
 def rb_filter_plain(desc, templates: torch.Tensor, strain: torch.Tensor, psd: torch.Tensor, capacity=1 << 20,

@@ -98,8 +98,9 @@ int make_geometry(const rb_filter_desc& d, Geometry* g) {
     set_detail("thresholds must be finite and >= 0");
     return RB_ERR_BAD_INPUT;
   }
-  if (d.cand_capacity < 0 || d.cand_capacity > INT32_MAX || d.reserved != 0) {
-    set_detail("cand_capacity must be in [0, 2^31) and reserved must be 0");
+  if (d.cand_capacity < 0 || d.cand_capacity > INT32_MAX ||
+      (d.mem & ~(RB_MEM_HOST_STRAIN | RB_MEM_HOST_TRIGGERS)) != 0) {
+    set_detail("cand_capacity must be in [0, 2^31) and mem may hold only RB_MEM_* bits");
     return RB_ERR_BAD_INPUT;
   }
   if (d.precision < RB_PREC_FP32 || d.precision > RB_PREC_FP16_SPLIT_A) {
@@ -177,14 +178,24 @@ using namespace rb;
 
 namespace {
 
+// Triggers rb_filter can stage on the device for a host trigger buffer: the four-step intermediate X
+// ([vc][n] complex) is idle from the end of the basis filter on.
+int64_t host_trig_capacity(const Geometry& g, const Workspace& ws) {
+  return (int64_t)(sizeof(float2) * (size_t)g.n * ws.vc / sizeof(rb_trigger));
+}
+
 int prepare(const rb_filter_desc* desc, void* workspace, size_t bytes, bool plain, Geometry* g, Workspace* ws,
-            cudaStream_t st) {
+            cudaStream_t st, bool host_buffers = false) {
   if (!desc) {
     set_detail("desc is NULL");
     return RB_ERR_BAD_INPUT;
   }
   int rc = make_geometry(*desc, g);
   if (rc) return rc;
+  if (desc->mem != 0 && !host_buffers) {
+    set_detail("desc->mem = %d: host buffers are taken by rb_filter only; this call wants 0", desc->mem);
+    return RB_ERR_BAD_INPUT;
+  }
   Workspace probe;
   carve(*desc, *g, nullptr, &probe, plain);
   if (!workspace || bytes < probe.total || ((uintptr_t)workspace & 255)) {
@@ -274,6 +285,10 @@ int batch_validate(const rb_filter_desc* descs, const rb_basis* bases, int32_t n
   int rc = batch_workspace(descs, n_bases, &out->geos, &need);
   if (rc) return rc;
   for (int32_t i = 0; i < n_bases; ++i) {
+    if (descs[i].mem != 0) {
+      set_detail("descs[%d].mem = %d: batch blocks take device pointers", i, descs[i].mem);
+      return RB_ERR_BAD_INPUT;
+    }
     if ((rc = check_basis(descs[i], &bases[i], true))) return rc;
     if (bases[i].coeff_op_precision != descs[i].precision) {
       set_detail("bases[%d] was packed for precision %d, descs[%d] asks for %d", i, bases[i].coeff_op_precision, i,
@@ -439,6 +454,7 @@ int rb_filter_plan(const rb_filter_desc* desc, rb_filter_sizes* out) {
   out->n2 = g.n2;
   out->kp = g.kp;
   out->coeff_op_bytes = coeff_op_bytes(*desc, g);
+  out->host_trig_capacity = host_trig_capacity(g, a);
   return RB_OK;
 }
 
@@ -626,15 +642,28 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
   cudaStream_t st = (cudaStream_t)stream;
   Geometry g;
   Workspace ws;
-  int rc = prepare(desc, workspace, workspace_bytes, false, &g, &ws, st);
+  int rc = prepare(desc, workspace, workspace_bytes, false, &g, &ws, st, true);
   if (rc) return rc;
   if ((rc = check_basis(*desc, basis, true))) return rc;
   if (!strain || !psd || !n_trig || capacity < 0 || (capacity > 0 && !trig)) {
     set_detail("NULL array or negative capacity");
     return RB_ERR_BAD_INPUT;
   }
+  // host buffers: the strain is staged in the beta region (written only after the whitening FFT
+  // has read it) and the triggers in the four-step intermediate (free once the basis filter is done)
+  const bool host_in = desc->mem & RB_MEM_HOST_STRAIN, host_out = desc->mem & RB_MEM_HOST_TRIGGERS;
+  if (host_out && capacity > host_trig_capacity(g, ws)) {
+    set_detail("capacity %lld exceeds host_trig_capacity %lld", (long long)capacity,
+               (long long)host_trig_capacity(g, ws));
+    return RB_ERR_BAD_INPUT;
+  }
+  rb_trigger* trig_d = host_out ? reinterpret_cast<rb_trigger*>(ws.X) : trig;
   StageMarks mk;
   mk.begin(st);
+  if (host_in) {
+    RB_CUDA_TRY(cudaMemcpyAsync(ws.beta, strain, sizeof(float) * g.n, cudaMemcpyHostToDevice, st));
+    strain = reinterpret_cast<const float*>(ws.beta);
+  }
   if ((rc = init_tables(g, ws, psd, desc->fs, st))) return rc;
   mk.to(RB_STAGE_WHITEN);
   if ((rc = whiten(g, ws, strain, ws.shat, st))) return rc;
@@ -646,10 +675,15 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
   mk.to(RB_STAGE_BUCKET);
   if ((rc = stage2_bucket(*desc, g, ws, 0, st))) return rc;
   mk.to(RB_STAGE_SECOND);
-  if ((rc = stage2_run(*desc, *basis, g, ws, ws.beta, trig, capacity, ws.trig_count, st))) return rc;
+  if ((rc = stage2_run(*desc, *basis, g, ws, ws.beta, trig_d, capacity, ws.trig_count, st))) return rc;
   mk.finish();
   Status s;
   if ((rc = read_status(ws, &s, st))) return rc;
+  if (host_out && s.trig > 0 && capacity > 0) {
+    const int64_t copied = std::min<int64_t>((int64_t)s.trig, capacity);
+    RB_CUDA_TRY(cudaMemcpyAsync(trig, trig_d, sizeof(rb_trigger) * copied, cudaMemcpyDeviceToHost, st));
+    RB_CUDA_TRY(cudaStreamSynchronize(st));
+  }
   if (s.flags & RB_FLAG_BAD_PSD) {
     set_detail("PSD not finite and positive on 0 < j < n/2");
     return RB_ERR_BAD_INPUT;
@@ -661,6 +695,147 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
   if ((int64_t)s.cand > desc->cand_capacity) {
     *n_trig = -1;
     set_detail("%llu first-stage candidates exceed cand_capacity %lld", s.cand, (long long)desc->cand_capacity);
+    return RB_ERR_OVERFLOW;
+  }
+  *n_trig = (int64_t)s.trig;
+  if ((int64_t)s.trig > capacity) {
+    set_detail("%llu triggers exceed capacity %lld", s.trig, (long long)capacity);
+    return RB_ERR_OVERFLOW;
+  }
+  return RB_OK;
+}
+
+int rb_banks_plan(const rb_filter_desc* descs, int32_t n_banks, rb_filter_sizes* out) {
+  if (!descs || !out || n_banks < 1) {
+    set_detail("NULL argument or n_banks < 1");
+    return RB_ERR_BAD_INPUT;
+  }
+  rb_filter_sizes s{};
+  int64_t host_cap = INT64_MAX;
+  for (int32_t b = 0; b < n_banks; ++b) {
+    Geometry g;
+    int rc = make_geometry(descs[b], &g);
+    if (rc) return rc;
+    if (descs[b].n != descs[0].n || descs[b].fs != descs[0].fs || descs[b].w != descs[0].w ||
+        descs[b].mem != descs[0].mem) {
+      set_detail("descs[%d] differs from descs[0] in n, fs, w or mem", b);
+      return RB_ERR_BAD_INPUT;
+    }
+    Workspace w;
+    carve(descs[b], g, nullptr, &w, false);
+    s.workspace_bytes = std::max(s.workspace_bytes, w.total);
+    s.n_bins = g.n_bins;
+    s.n1 = g.n1;
+    s.n2 = g.n2;
+    s.kp = std::max(s.kp, g.kp);
+    host_cap = std::min(host_cap, host_trig_capacity(g, w));
+  }
+  s.coeff_op_bytes = 0;
+  s.host_trig_capacity = host_cap;
+  *out = s;
+  return RB_OK;
+}
+
+int rb_filter_banks(const rb_filter_desc* descs, const rb_basis* bases, int32_t n_banks, const float* strain,
+                    const double* psd, rb_trigger* trig, int64_t capacity, int64_t* n_trig, void* workspace,
+                    size_t workspace_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  rb_filter_sizes plan;
+  int rc = rb_banks_plan(descs, n_banks, &plan);
+  if (rc) return rc;
+  if (!bases || !strain || !psd || !n_trig || capacity < 0 || (capacity > 0 && !trig)) {
+    set_detail("NULL array or negative capacity");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (!workspace || workspace_bytes < plan.workspace_bytes || ((uintptr_t)workspace & 255)) {
+    set_detail("workspace %p of %zu bytes; need %zu bytes, 256-byte aligned", workspace, workspace_bytes,
+               plan.workspace_bytes);
+    return RB_ERR_OOM;
+  }
+  int64_t rows = 0;
+  for (int32_t b = 0; b < n_banks; ++b) {
+    if ((rc = check_basis(descs[b], &bases[b], true))) return rc;
+    if (bases[b].coeff_op_precision != descs[b].precision) {
+      set_detail("bases[%d] was packed for precision %d, descs[%d] asks for %d", b, bases[b].coeff_op_precision, b,
+                 descs[b].precision);
+      return RB_ERR_BAD_INPUT;
+    }
+    rows += descs[b].n_templates;
+  }
+  if (rows > INT32_MAX) {
+    set_detail("the sub-banks hold %lld templates in all (at most 2^31 - 1)", (long long)rows);
+    return RB_ERR_BAD_INPUT;
+  }
+  const bool host_in = descs[0].mem & RB_MEM_HOST_STRAIN, host_out = descs[0].mem & RB_MEM_HOST_TRIGGERS;
+  if (host_out && capacity > plan.host_trig_capacity) {
+    set_detail("capacity %lld exceeds host_trig_capacity %lld", (long long)capacity,
+               (long long)plan.host_trig_capacity);
+    return RB_ERR_BAD_INPUT;
+  }
+  // every carving shares the status block, the tables, the whitening weights and s_hat (their offsets
+  // depend on n only), so the block is whitened once; the rest is per sub-bank scratch
+  Geometry g0;
+  Workspace ws0;
+  if ((rc = make_geometry(descs[0], &g0))) return rc;
+  carve(descs[0], g0, (char*)workspace, &ws0, false);
+  RB_CUDA_TRY(cudaMemsetAsync(ws0.flags, 0, 256, st));
+  rb_trigger* trig_d = host_out ? reinterpret_cast<rb_trigger*>(ws0.X) : trig;
+  StageMarks mk;
+  mk.begin(st);
+  if (host_in) {
+    RB_CUDA_TRY(cudaMemcpyAsync(ws0.beta, strain, sizeof(float) * g0.n, cudaMemcpyHostToDevice, st));
+    strain = reinterpret_cast<const float*>(ws0.beta);
+  }
+  if ((rc = init_tables(g0, ws0, psd, descs[0].fs, st))) return rc;
+  mk.to(RB_STAGE_WHITEN);
+  if ((rc = whiten(g0, ws0, strain, ws0.shat, st))) return rc;
+  int64_t copied = 0, base = 0;
+  Status s{};
+  for (int32_t b = 0; b < n_banks; ++b) {
+    rb_filter_desc d = descs[b];
+    d.sample_offset = descs[0].sample_offset;
+    d.block_id = descs[0].block_id;
+    Geometry g;
+    Workspace ws;
+    make_geometry(d, &g);
+    carve(d, g, (char*)workspace, &ws, false);
+    // profiling: one event set per sub-bank (the first also holds the set-up and the whitening), so
+    // the per-stage means of rb_profile_stop times n_banks are the per-call totals
+    if (b > 0) mk.begin(st);
+    RB_CUDA_TRY(cudaMemsetAsync(ws.cand_count, 0, sizeof(unsigned long long), st));
+    mk.to(RB_STAGE_BASIS);
+    if ((rc = bank_filter(g, ws, (const float2*)bases[b].vectors, d.k, ws.shat, ws.beta, ws.bavg, d.w, st))) return rc;
+    mk.to(RB_STAGE_PACK);
+    if ((rc = run_stage1(d, bases[b], g, ws, ws.bavg, ws.cand, st, &mk))) return rc;
+    mk.to(RB_STAGE_BUCKET);
+    if ((rc = stage2_bucket(d, g, ws, 0, st))) return rc;
+    mk.to(RB_STAGE_SECOND);
+    if ((rc = stage2_run(d, bases[b], g, ws, ws.beta, trig_d, capacity, ws.trig_count, st, (int)base))) return rc;
+    mk.finish();
+    base += d.n_templates;
+    if (host_out) {
+      // the staging area is the next sub-bank's four-step intermediate: copy this sub-bank's triggers
+      // out (stream-ordered before that sub-bank's basis filter) once their count is known
+      if ((rc = read_status(ws0, &s, st))) return rc;
+      const int64_t upto = std::min<int64_t>((int64_t)s.trig, capacity);
+      if (upto > copied)
+        RB_CUDA_TRY(cudaMemcpyAsync(trig + copied, trig_d + copied, sizeof(rb_trigger) * (upto - copied),
+                                    cudaMemcpyDeviceToHost, st));
+      copied = std::max(copied, upto);
+    }
+  }
+  if ((rc = read_status(ws0, &s, st))) return rc;
+  if (s.flags & RB_FLAG_BAD_PSD) {
+    set_detail("PSD not finite and positive on 0 < j < n/2");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (s.flags & RB_FLAG_TIMEOUT) {
+    set_detail("a bounded device-side wait (tcgen05 first or second stage) timed out");
+    return RB_ERR_TIMEOUT;
+  }
+  if (s.flags & RB_FLAG_CAND_OVERFLOW) {
+    *n_trig = -1;
+    set_detail("a sub-bank had more first-stage candidates than its desc's cand_capacity");
     return RB_ERR_OVERFLOW;
   }
   *n_trig = (int64_t)s.trig;

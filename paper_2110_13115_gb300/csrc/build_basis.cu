@@ -366,9 +366,57 @@ int orthonormalise(int l, int64_t half, const BuildWs& w, float2*& Y, float2*& Q
   return RB_OK;
 }
 
+// Largest single-template truncation loss for every basis size: loss[q] = max_t (1 - sum_{j<=q} |a_tj|^2),
+// accumulated in FP64, clamped at 0 (rounding can push the captured fraction of a row slightly above
+// one). Non-negative doubles order like their bit patterns, so the maxima are unsigned 64-bit atomics:
+// one shared-memory maximum per CTA and basis size, then one global atomic per (CTA, size).
+__global__ void __launch_bounds__(256) k_max_loss(const float2* __restrict__ coeff, int T, int k,
+                                                  unsigned long long* __restrict__ out) {
+  extern __shared__ unsigned long long smax[];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) smax[q] = 0ull;
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < T) {
+    const float2* row = coeff + (int64_t)t * k;
+    double cap = 0.0;
+    for (int q = 0; q < k; ++q) {
+      const float2 a = row[q];
+      cap += (double)a.x * a.x + (double)a.y * a.y;
+      const double loss = fmax(1.0 - cap, 0.0);
+      atomicMax(&smax[q], (unsigned long long)__double_as_longlong(loss));
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < k; q += blockDim.x) atomicMax(&out[q], smax[q]);
+}
+
 }  // namespace
 
 extern "C" {
+
+int rb_basis_max_loss(const rb_basis* basis, double* loss, void* workspace, size_t workspace_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!basis || !basis->coeff || !loss || basis->k < 1 || basis->n_templates < 1) {
+    rb::set_detail("NULL basis, coefficients or output, or k, T < 1");
+    return RB_ERR_BAD_INPUT;
+  }
+  const int k = basis->k, T = basis->n_templates;
+  if ((size_t)k * 8 > 48 * 1024) {
+    rb::set_detail("k = %d above the %d vectors this call handles", k, 48 * 1024 / 8);
+    return RB_ERR_UNSUPPORTED;
+  }
+  if (!workspace || workspace_bytes < (size_t)k * 8 || ((uintptr_t)workspace & 255)) {
+    rb::set_detail("workspace too small: need %zu bytes, 256-byte aligned", (size_t)k * 8);
+    return RB_ERR_OOM;
+  }
+  auto* acc = (unsigned long long*)workspace;
+  RB_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)k * 8, st));
+  k_max_loss<<<(T + 255) / 256, 256, (size_t)k * 8, st>>>((const float2*)basis->coeff, T, k, acc);
+  RB_LAUNCH_CHECK();
+  RB_CUDA_TRY(cudaMemcpyAsync(loss, acc, (size_t)k * 8, cudaMemcpyDeviceToHost, st));
+  RB_CUDA_TRY(cudaStreamSynchronize(st));
+  return RB_OK;
+}
 
 int rb_build_plan(const rb_bank_desc* bank, int32_t k, int32_t oversample, size_t* templates_bytes,
                   size_t* build_bytes) {

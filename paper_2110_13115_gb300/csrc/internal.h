@@ -100,11 +100,14 @@ int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& 
                     cudaStream_t st);
 // tcgen05 second stage (w <= 8; RB_ERR_UNSUPPORTED when k does not fit) and its selection
 int stage2_tc_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-                  const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st);
+                  const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st,
+                  int tmpl_base = 0);
 bool stage2_use_tc();
 // The two halves of stage2_bucketed: bucketing of ws.cand by bin, then the reconstruction.
 int stage2_bucket(const rb_filter_desc& d, const Geometry& g, const Workspace& ws, int bin_lo, cudaStream_t st);
+// tmpl_base is added to every trigger's template row (sub-banks filtered into one list).
 int stage2_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-               const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st);
+               const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st,
+               int tmpl_base = 0);
 
 }  // namespace rb

@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
                                                      const unsigned* __restrict__ piece_total,
                                                      const rb::SortedCand* __restrict__ sorted, float thr2,
                                                      int64_t sample_offset, rb_trigger* __restrict__ trig,
-                                                     unsigned long long* counter, int64_t cap) {
+                                                     unsigned long long* counter, int64_t cap, int tmpl_base) {
   constexpr int NT = S2<W>::NT;
   extern __shared__ __align__(16) uint8_t s2mem[];
   const int pitch = k16 + 1;                        // padded window rows (bank spread)
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
           if ((int64_t)idx < cap) {
             rb_trigger tg;
             tg.sample = sample_offset + (int64_t)(bin0 + b) * W + br;
-            tg.tmpl = cd.tmpl;
+            tg.tmpl = tmpl_base + cd.tmpl;
             tg.block = cd.block;
             tg.snr = sqrtf(best);
             tg.phase = atan2f(zi, zr);
@@ -451,7 +451,8 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
 
 template <int W>
 int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
-                const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st) {
+                const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, int tmpl_base,
+                cudaStream_t st) {
   constexpr int NT = S2<W>::NT;
   const int nb = (int)g.n_bins;
   const int k16 = (d.k + 15) / 16 * 16;
@@ -467,7 +468,7 @@ int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& 
   const __half* ahi = reinterpret_cast<const __half*>(b.coeff_op);
   const __half* alo = ahi + (int64_t)d.n_templates * 2 * k16;
   kern<<<grid, 256, smem, st>>>(ahi, alo, beta, d.k, k16, d.n_templates, g.n / 2, nb, ws.pieces, ws.piece_total,
-                                ws.cand_sorted, d.rho_ii * d.rho_ii, d.sample_offset, trig, counter, cap);
+                                ws.cand_sorted, d.rho_ii * d.rho_ii, d.sample_offset, trig, counter, cap, tmpl_base);
   RB_LAUNCH_CHECK();
   return RB_OK;
 }
@@ -492,17 +493,18 @@ int stage2_bucket(const rb_filter_desc& d, const Geometry& g, const Workspace& w
 }
 
 int stage2_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-               const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st) {
+               const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st,
+               int tmpl_base) {
   if (stage2_use_tc() && d.w <= 8) {
-    const int rc = stage2_tc_run(d, b, g, ws, beta, trig, cap, counter, st);
+    const int rc = stage2_tc_run(d, b, g, ws, beta, trig, cap, counter, st, tmpl_base);
     if (rc != RB_ERR_UNSUPPORTED) return rc;
   }
   switch (d.w) {
-    case 1: return launch_bins<1>(d, b, g, ws, beta, trig, cap, counter, st);
-    case 2: return launch_bins<2>(d, b, g, ws, beta, trig, cap, counter, st);
-    case 4: return launch_bins<4>(d, b, g, ws, beta, trig, cap, counter, st);
-    case 8: return launch_bins<8>(d, b, g, ws, beta, trig, cap, counter, st);
-    case 16: return launch_bins<16>(d, b, g, ws, beta, trig, cap, counter, st);
+    case 1: return launch_bins<1>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
+    case 2: return launch_bins<2>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
+    case 4: return launch_bins<4>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
+    case 8: return launch_bins<8>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
+    case 16: return launch_bins<16>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
   }
   return RB_ERR_BAD_INPUT;
 }

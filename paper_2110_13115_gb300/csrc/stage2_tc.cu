@@ -68,6 +68,7 @@ struct S2Params {
   unsigned* flags;
   uint32_t idesc;
   int withhold_copies;  // failure-detection test: the producers issue no copy (rbx_stage2_withhold_copies)
+  int tmpl_base;        // added to a trigger's template row (sub-banks filtered into one list)
 };
 
 // Packed column order of rb_pack_coeff: position p = 32 q + 8 t4 + s holds column
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
           if ((int64_t)idx < p.cap) {
             rb_trigger tg;
             tg.sample = p.sample_offset + (int64_t)(p.bin0 + bin) * W + br;
-            tg.tmpl = cd.tmpl;
+            tg.tmpl = p.tmpl_base + cd.tmpl;
             tg.block = cd.block;
             tg.snr = sqrtf(best);
             tg.phase = atan2f(zi, zr);
@@ -397,8 +398,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
 template <int W, int N>
 int launch_tc2(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
                const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st,
-               int withhold) {
+               int withhold, int tmpl_base) {
   S2Params p;
+  p.tmpl_base = tmpl_base;
   p.k16 = (int)g.k16;
   p.k = d.k;
   p.kp2 = (2 * p.k16 + kKB - 1) / kKB * kKB;
@@ -441,16 +443,17 @@ std::atomic<int> g_withhold2{0};  // launches left whose producers issue no copy
 namespace rb {
 
 int stage2_tc_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
-                  const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st) {
+                  const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st,
+                  int tmpl_base) {
   int left = g_withhold2.load();
   while (left > 0 && !g_withhold2.compare_exchange_weak(left, left - 1)) {
   }
   const int withhold = left > 0 ? 1 : 0;
   switch (d.w) {
-    case 1: return launch_tc2<1, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold);
-    case 2: return launch_tc2<2, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold);
-    case 4: return launch_tc2<4, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold);
-    case 8: return launch_tc2<8, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold);
+    case 1: return launch_tc2<1, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold, tmpl_base);
+    case 2: return launch_tc2<2, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold, tmpl_base);
+    case 4: return launch_tc2<4, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold, tmpl_base);
+    case 8: return launch_tc2<8, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold, tmpl_base);
   }
   set_detail("the tensor-core second stage takes w <= 8");
   return RB_ERR_UNSUPPORTED;

@@ -280,12 +280,13 @@ def precision(k: int = 400, w: int = 8, n_templates: int = 50000, n_inj: int = 3
 
 def scaled(name: str, fs: float, n: int, n_templates: int, m_range=(3.0, 50.0), chi_max=0.5, pn_order=3,
            f_low=30.0, k=64, w=8, n_inj=2, snr_range=(8.0, 15.0), rho_ii=5.0, min_sep=1.0,
-           segment=0, detector=0, psd_scale=1.0) -> Workload:
-    """A workload with the full-size recipe at a smaller block and bank (parity cases)."""
+           segment=0, detector=0, psd_scale=1.0, noise=True) -> Workload:
+    """A workload with the full-size recipe at a smaller block and bank (parity cases); noise=False
+    leaves the injections alone in the block."""
     grid = Grid(fs=fs, n=n, f_low=f_low)
     spec = BankSpec(n_templates, m_range[0], m_range[1], chi_max, pn_order)
     return make_workload(name, grid, spec, k=k, w=w, rho_ii=rho_ii, n_inj=n_inj, snr_range=snr_range,
-                         min_sep=min_sep, segment=segment, detector=detector, psd_scale=psd_scale)
+                         min_sep=min_sep, segment=segment, detector=detector, psd_scale=psd_scale, noise=noise)
 
 
 # --- batches of uneven segments from two detectors ----------------------------------------
