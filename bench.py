@@ -43,7 +43,14 @@ def parse():
     # 1e-3 band around rho_I, and every reported SNR comes from the FP32-accurate second stage
     p.add_argument("--precision", default="fp16_split_a")
     p.add_argument("--w", type=int, default=8)
-    p.add_argument("--k", type=int, default=256)
+    # the bank is cut into sub-banks of equal template count along tau0 (Sec. III.B, Table I), each with
+    # the fewest basis vectors that hold every template's SNR loss within --tol
+    p.add_argument("--subbanks", type=int, default=4)
+    p.add_argument("--tol", type=float, default=1e-3, help="largest single-template SNR loss of a sub-bank basis")
+    p.add_argument("--k-build", type=int, default=320, help="basis vectors built per sub-bank before truncation")
+    p.add_argument("--k", type=int, default=None, help="fixed basis size per sub-bank (skips the tolerance)")
+    p.add_argument("--batch-segments", type=int, default=64,
+                   help="segments of the batching workload reported under 'batch' (0: skip it)")
     p.add_argument("--templates", type=int, default=10000)
     p.add_argument("--n", type=int, default=524288)
     p.add_argument("--recovery", type=float, default=0.99)
@@ -119,7 +126,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = inputs.full(w=args.w, k=args.k, n_templates=args.templates, n=args.n)
+    wl = inputs.full(w=args.w, k=args.k or 256, n_templates=args.templates, n=args.n)
     cores = len(os.sched_getaffinity(0))
     ctx = mp.get_context("spawn")
     g = wl.grid
@@ -220,27 +227,34 @@ def traffic_from_profiles(kernel_key, src_hash):
     return d.get("dram_bytes_per_launch")
 
 
-def calibrate_rho_i(api, basis, templates, psd_d, wl_cal, args, torch):
+def calibrate_rho_i(api, subs, templates, psd_d, wl_cal, args, torch):
     """Largest rho_I with n_final >= recovery * n_flat at rho_II on a noise-only block (Eq. 16):
-    the (1 - recovery) quantile of the bin-averaged SNR over the bins of the flat triggers."""
+    the (1 - recovery) quantile of the bin-averaged SNR over the bins of the flat triggers, with the
+    bin-averaged SNR computed by the first stage of every sub-bank in the run's own precision."""
     g = wl_cal.grid
-    T = len(wl_cal.bank)
+    T = sum(sb["T"] for sb in subs)
     strain = torch.from_numpy(wl_cal.strain).cuda()
-    dp = api.make_desc(g.fs, g.n, args.k, T, w=args.w, rho_ii=wl_cal.rho_ii)
+    dp = api.make_desc(g.fs, g.n, 1, T, w=args.w, rho_ii=wl_cal.rho_ii)
     buf, nflat = api.rb_filter_plain(dp, templates, strain, psd_d, capacity=1 << 22)
     flat = api.triggers_numpy(buf, nflat)
     if nflat == 0:
         return 3.0, 0
     probe = 3.0
+    for sb in subs:  # the screen is calibrated in the first-stage precision that the timed run uses
+        api.rb_pack_coeff(api.make_desc(g.fs, g.n, sb["basis"].k, sb["T"], w=args.w, precision=args.precision),
+                          sb["basis"])
     while True:
-        d = api.make_desc(g.fs, g.n, args.k, T, w=args.w, precision="fp32", rho_i=probe, cand_capacity=1 << 26)
-        ws = api.workspace(d)
-        sh = api.rb_whiten(d, strain, psd_d, ws=ws)
-        _, bavg = api.rb_basis_filter(d, basis, sh, keep_beta=False, ws=ws)
-        cand, nc = api.rb_stage1(d, basis, bavg, ws=ws)
-        cands = api.candidates_numpy(cand, nc)
-        del ws, cand, bavg
-        look = {(int(c["tmpl"]), int(c["bin"])): float(c["snr_avg"]) for c in cands}
+        look = {}
+        for sb in subs:
+            d = api.make_desc(g.fs, g.n, sb["basis"].k, sb["T"], w=args.w, precision=args.precision, rho_i=probe,
+                              cand_capacity=1 << 26)
+            ws = api.workspace(d)
+            sh = api.rb_whiten(d, strain, psd_d, ws=ws)
+            _, bavg = api.rb_basis_filter(d, sb["basis"], sh, keep_beta=False, ws=ws)
+            cand, nc = api.rb_stage1(d, sb["basis"], bavg, ws=ws)
+            for c in api.candidates_numpy(cand, nc):
+                look[(sb["base"] + int(c["tmpl"]), int(c["bin"]))] = float(c["snr_avg"])
+            del ws, cand, bavg, sh
         vals = np.array([look.get((int(t["tmpl"]), int(t["sample"]) // args.w), 0.0) for t in flat])
         # bins below the probe threshold are unknown (0); the quantile is exact once it sits above it
         q = float(np.quantile(vals, 1.0 - args.recovery, method="lower"))
@@ -249,19 +263,59 @@ def calibrate_rho_i(api, basis, templates, psd_d, wl_cal, args, torch):
         probe -= 0.5
 
 
-def accuracy(rb_trig, plain_trig, w, rho_ii):
-    """Relative SNR loss of the hierarchy against the template method on the same GPU and block."""
+def noise_accuracy(rb_trig, plain_trig, w, rho_ii):
+    """Trigger-level comparison of the hierarchy with the template method on the same GPU and block."""
     p = {(int(t["tmpl"]), int(t["sample"]) // w): float(t["snr"]) for t in plain_trig}
     r = {(int(t["tmpl"]), int(t["sample"]) // w): float(t["snr"]) for t in rb_trig}
     matched = [(p[k], r[k]) for k in p if k in r]
-    loss = [(a - b) / a for a, b in matched]
+    err = [(b - a) / a for a, b in matched]
     # triggers of the flat search that the hierarchy missed although clearly above threshold
     missed_clear = sum(1 for k, v in p.items() if k not in r and v > rho_ii * 1.001)
     return dict(n_flat=len(p), n_hier=len(r), matched=len(matched),
                 recovery=(len(matched) / len(p)) if p else 1.0,
-                max_rel_snr_loss=max(loss) if loss else 0.0,
-                max_abs_rel_snr_err=max(abs(x) for x in loss) if loss else 0.0,
-                missed_above_threshold=missed_clear)
+                max_abs_rel_snr_err=max(abs(x) for x in err) if err else 0.0,
+                rms_rel_snr_err=float(np.sqrt(np.mean(np.square(err)))) if err else 0.0,
+                missed_above_threshold=missed_clear,
+                note="in noise the reduced-basis SNR differs from the template method's by the noise in the "
+                     "discarded basis directions, about r_t/rho relative (r_t^2 = the template's truncation "
+                     "loss); the paper's Fig. relative_error shows ~0.4 % at SNR 5")
+
+
+def injection_snrs(api, torch, wl, subs, rows, templates, psd_d, args, rho_i, rho_ii, descs_for):
+    """Per injection: the best template of the template method near its coalescence time (GPU), that
+    template's SNR from the FP64 oracle's template method (mf.snr_series) in the same window, and the
+    hierarchical SNR of the same (template, window). Returns a list of dicts."""
+    from oracle import mf, waveform as W
+
+    g = wl.grid
+    T = len(rows)
+    strain = torch.from_numpy(wl.strain).cuda()
+    descs, bases = descs_for(rho_i, rho_ii)
+    buf, n = api.rb_filter_banks(descs, bases, strain, psd_d, capacity=1 << 23)
+    hier = {(int(t["tmpl"]), int(t["sample"]) // args.w): float(t["snr"]) for t in api.triggers_numpy(buf, n)}
+    dp = api.make_desc(g.fs, g.n, 1, T, w=args.w, rho_ii=rho_ii)
+    pbuf, pn = api.rb_filter_plain(dp, templates, strain, psd_d, capacity=1 << 23)
+    flat = api.triggers_numpy(pbuf, pn)
+    s_fd = mf.strain_fd(wl.strain.astype(np.float64), g.fs)
+    out = []
+    for inj in wl.injections:
+        m_c = int(round(inj.tc * g.fs))
+        near = flat[np.abs(flat["sample"] - m_c) <= int(0.05 * g.fs)]
+        if len(near) == 0:
+            out.append(dict(snr_opt=inj.snr, found=False))
+            continue
+        best = near[np.argmax(near["snr"])]
+        r, b = int(best["tmpl"]), int(best["sample"]) // args.w
+        h = W.template(wl.bank[rows[r]], g.fs, g.n, g.f_low, wl.bank_spec.pn_order)
+        z, sig = mf.snr_series(s_fd, h, wl.psd, g.n, g.fs)
+        rho_flat = float(np.abs(z[b * args.w:(b + 1) * args.w]).max() / sig)
+        rho_rb = hier.get((r, b))
+        sb = next(x for x in subs if x["base"] <= r < x["base"] + x["T"])
+        loss_t = float(sb["template_loss"][r - sb["base"]])
+        out.append(dict(snr_opt=round(inj.snr, 3), template=r, snr_oracle=rho_flat, snr_hier=rho_rb,
+                        rel_loss=None if rho_rb is None else (rho_flat - rho_rb) / rho_flat,
+                        template_truncation_loss=loss_t))
+    return out
 
 
 def cufft_comparator(torch, templates, s_hat, n, w, rho_ii, secs, sample=512, chunk=32, reps=3):
@@ -362,7 +416,7 @@ def refine_rate(api, torch, n_cand=1024, steps=20, reps=3):
                 workload="tiny: 64-template bank, 16-s block at 1024 Hz, one injection")
 
 
-def run_batch(args):
+def batch_measure(args, n_segments, steps, warmup, dist=None):
     """Batch workload: 64 segments of 32-512 s at 2048 Hz seen by two detectors (independent Gaussian
     noise, PSD scale factors 0.5-2), blocks of min(128 s, 2^floor(log2 L)) with half overlap (FFT sizes
     2^16-2^18), four banks of 5k-20k templates concatenated over one k = 256 basis per FFT size.
@@ -374,17 +428,11 @@ def run_batch(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _native.load()
+    k = args.k or 256  # the batching workload shares one k = 256 basis per FFT size
     # noise only, as in the paper's throughput runs (the batch tests inject signals); every rank
     # filters its own segments (independent replicas)
-    wl = inputs.batch(n_segments=args.segments, k=args.k, w=args.w, seed=4 + rank, inj_per_segment=0)
+    wl = inputs.batch(n_segments=n_segments, k=k, w=args.w, seed=4 + rank, inj_per_segment=0)
     bank = wl.bank
     T = len(bank)
     rho_i = 4.373 if args.rho_i is None else args.rho_i
@@ -392,9 +440,9 @@ def run_batch(args):
     descs, bases, where = [], [], {}
     for i, n in enumerate(wl.sizes):
         psd1 = torch.from_numpy(inputs.analytic_psd(inputs.Grid(wl.fs, n, wl.f_low))).cuda()
-        b = api.rb_build(api.Bank(bank, wl.fs, n, wl.f_low, wl.bank_spec.pn_order), psd1, args.k, oversample=64,
+        b = api.rb_build(api.Bank(bank, wl.fs, n, wl.f_low, wl.bank_spec.pn_order), psd1, k, oversample=64,
                          power_iters=1)
-        d = api.make_desc(wl.fs, n, args.k, T, w=args.w, precision=args.precision, rho_i=rho_i, rho_ii=wl.rho_ii,
+        d = api.make_desc(wl.fs, n, k, T, w=args.w, precision=args.precision, rho_i=rho_i, rho_ii=wl.rho_ii,
                           cand_capacity=1 << 25)
         api.rb_pack_coeff(d, b)
         descs.append(d)
@@ -437,47 +485,107 @@ def run_batch(args):
         del sh
     cap = 1 << 25
     batch = api.Batch(descs, bases, blocks, capacity=cap, ws=ws)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = api.rb_kernel_launches()
     with Clocks(local) as clk:
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             _, nt = batch.run()
         e1.record()
         torch.cuda.synchronize()
-    launches = (api.rb_kernel_launches() - l0) // max(args.steps, 1)
+    launches = (api.rb_kernel_launches() - l0) // max(steps, 1)
     tsec = T * wl.valid_seconds
-    ms, value = replicas.job_rate(tsec, e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    ms, value = replicas.job_rate(tsec, e0.elapsed_time(e1) / steps, dist, "cuda")
     # end to end: each step copies every block from pinned host memory, replays, reads the triggers
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     d2h = 0
-    for _ in range(args.steps):
+    for _ in range(steps):
         dev.copy_(host, non_blocking=True)
         tb, n2 = batch.run()
         out = tb[: n2 * 24].cpu()
         d2h += out.numel()
     torch.cuda.synchronize()
-    e2e_ms, e2e_value = replicas.job_rate(tsec, (time.perf_counter() - t1) * 1e3 / args.steps, dist, "cuda")
+    e2e_ms, e2e_value = replicas.job_rate(tsec, (time.perf_counter() - t1) * 1e3 / steps, dist, "cuda")
     batch.close()
-    res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+    res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=steps, warmup=warmup,
                ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
                data="synthetic",
-               config=dict(workload=wl.name, segments=args.segments, detectors=2, blocks=len(wl.blocks),
+               config=dict(workload=wl.name, segments=n_segments, detectors=2, blocks=len(wl.blocks),
                            fft_sizes=wl.sizes, templates=T, banks=[len(b) for b in wl.banks],
-                           valid_seconds=wl.valid_seconds, k=args.k, w=args.w, rho_I=rho_i, rho_II=wl.rho_ii,
+                           valid_seconds=wl.valid_seconds, k=k, w=args.w, rho_I=rho_i, rho_II=wl.rho_ii,
                            first_stage=args.precision, graph="one CUDA graph replay per step", tuned=tuned,
                            l2="inputs larger than L2: the bases alone are >= 134 MB each"),
                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=tot * 4,
-                        d2h_bytes_per_step=d2h // max(args.steps, 1)),
+                        d2h_bytes_per_step=d2h // max(steps, 1)),
                gpu_launches=int(launches), clocks=clk.summary(), build_s=build_s, n_triggers=int(nt))
-    if rank == 0:
+    del batch, ws, dev, bases, descs
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_batch(args):
+    """Batch workload: 64 segments of 32-512 s at 2048 Hz seen by two detectors (independent Gaussian
+    noise, PSD scale factors 0.5-2), blocks of min(128 s, 2^floor(log2 L)) with half overlap (FFT sizes
+    2^16-2^18), four banks of 5k-20k templates concatenated over one k = 256 basis per FFT size.
+    One step = one replay of the CUDA graph that filters every block (rb_batch_run)."""
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    res = batch_measure(args, args.segments, args.steps, args.warmup, dist)
+    if int(os.environ.get("RANK", "0")) == 0:
         print(json.dumps(res))
     if dist:
         dist.destroy_process_group()
+
+
+def build_subbanks(api, torch, wl, psd_d, args):
+    """The bank cut into args.subbanks parts of equal template count in ascending tau0 (Sec. III.B); each
+    part gets a GPU basis (rb_build) truncated to the fewest vectors that hold every template's SNR loss
+    within args.tol (rb_basis_max_loss), or to args.k when given."""
+    g = wl.grid
+    pn = wl.bank_spec.pn_order
+    bank = api.Bank(wl.bank, g.fs, g.n, g.f_low, pn)
+    order, offs = api.rb_bank_split_tau0(api.rb_bank_tau0(bank, g.f_low), max(args.subbanks, 1))
+    subs, base = [], 0
+    for p in range(max(args.subbanks, 1)):
+        idx = order[offs[p]:offs[p + 1]]
+        t0 = time.perf_counter()
+        kb = min(args.k or args.k_build, len(idx))
+        full = api.rb_build(api.Bank(np.ascontiguousarray(wl.bank[idx]), g.fs, g.n, g.f_low, pn), psd_d, kb,
+                            oversample=64, power_iters=1)
+        loss = api.rb_basis_max_loss(full)
+        if args.k:
+            k = kb
+        else:
+            ok = np.nonzero(loss <= args.tol)[0]
+            if len(ok) == 0:
+                raise SystemExit(f"sub-bank {p}: {kb} vectors leave a template loss of {loss[-1]:.2e} > {args.tol}; "
+                                 f"raise --k-build or --subbanks")
+            k = int(ok[0]) + 1
+        b = api.truncate(full, k)
+        cap = b.coeff.abs().pow(2).double().sum(1)
+        del full
+        torch.cuda.synchronize()
+        sv = b.singular_values
+        subs.append(dict(idx=idx, T=len(idx), base=base, basis=b, k=k, max_loss=float(loss[k - 1]),
+                         template_loss=(1.0 - cap).clamp(min=0).cpu().numpy(),
+                         eq8_loss=float(1.0 - np.sum(sv[:k] ** 2) / len(idx)),
+                         build_s=time.perf_counter() - t0))
+        base += len(idx)
+        torch.cuda.empty_cache()
+    return subs
 
 
 def main():
@@ -495,7 +603,7 @@ def main():
     # the CPU baseline's process pool starts before the first GPU call
     from paper_2110_13115_gb300 import inputs
 
-    wl = inputs.full(w=args.w, k=args.k, n_templates=args.templates, n=args.n, segment=rank)
+    wl = inputs.full(w=args.w, k=args.k or 256, n_templates=args.templates, n=args.n, segment=rank)
     pool, cores = None, 0
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = len(os.sched_getaffinity(0))
@@ -520,53 +628,64 @@ def main():
     T = len(wl.bank)
     psd_d = torch.from_numpy(wl.psd).cuda()
     strain_d = torch.from_numpy(wl.strain).cuda()
-    bank = api.Bank(wl.bank, g.fs, g.n, g.f_low, wl.bank_spec.pn_order)
 
     t0 = time.perf_counter()
-    basis = api.rb_build(bank, psd_d, args.k, oversample=64, power_iters=1)
-    torch.cuda.synchronize()
+    subs = build_subbanks(api, torch, wl, psd_d, args)
     build_s = time.perf_counter() - t0
-    captured = basis.coeff.abs().pow(2).double().cumsum(1)
-    trunc = 1.0 - captured[:, -1]
-    loss_by_k = {int(kk): float(1.0 - captured[:, kk - 1].min()) for kk in (64, 128, 192, 256, 320, 384, 448, 512)
-                 if kk <= args.k}
+    rows = np.concatenate([sb["idx"] for sb in subs])  # trigger template row -> bank template
+    P = len(subs)
     need_templates = not args.no_plain or args.rho_i is None
-    templates = api.rb_templates(bank, psd_d)[0] if need_templates else None
+    templates = None
+    if need_templates:
+        templates = api.rb_templates(api.Bank(np.ascontiguousarray(wl.bank[rows]), g.fs, g.n, g.f_low,
+                                              wl.bank_spec.pn_order), psd_d)[0]
 
     if args.rho_i is None:
-        wl_cal = inputs.full(w=args.w, k=args.k, n_templates=args.templates, n=args.n, segment=1000 + rank, n_inj=0)
-        rho_i, n_cal = calibrate_rho_i(api, basis, templates, psd_d, wl_cal, args, torch)
+        wl_cal = inputs.full(w=args.w, k=args.k or 256, n_templates=args.templates, n=args.n, segment=1000 + rank,
+                             n_inj=0)
+        rho_i, n_cal = calibrate_rho_i(api, subs, templates, psd_d, wl_cal, args, torch)
     else:
         rho_i, n_cal = args.rho_i, 0
 
-    d = api.make_desc(g.fs, g.n, args.k, T, w=args.w, precision=args.precision, rho_i=rho_i, rho_ii=wl.rho_ii,
-                      cand_capacity=1 << 25, sample_offset=0, block_id=rank)
-    ws = api.workspace(d)
-    tuned = None
-    api.rb_pack_coeff(d, basis)
-    # autotune the FFT schedule and the first stage's tile variant on this block (setup, untimed)
-    sh = api.rb_whiten(d, strain_d, psd_d, ws=ws)
+    def descs_for(ri, rii, cap_c=1 << 25):
+        ds = []
+        for sb in subs:
+            d = api.make_desc(g.fs, g.n, sb["k"], sb["T"], w=args.w, precision=args.precision, rho_i=ri, rho_ii=rii,
+                              cand_capacity=cap_c, sample_offset=0, block_id=rank)
+            ds.append(d)
+        return ds, [sb["basis"] for sb in subs]
+
+    descs, bases = descs_for(rho_i, wl.rho_ii)
+    for d, sb in zip(descs, subs):
+        api.rb_pack_coeff(d, sb["basis"])
+    ws = api.banks_workspace(descs)
+    # autotune the FFT schedule (shared by every sub-bank of this n and w) and each sub-bank's
+    # first-stage tile (setup, untimed)
+    sh = api.rb_whiten(descs[0], strain_d, psd_d, ws=ws)
+    big = max(range(P), key=lambda i: subs[i]["k"])
     if args.fft_variant is None:
-        fft_choice, fft_times = api.rb_tune_fft(d, basis, sh, ws=ws)
+        fft_choice, fft_times = api.rb_tune_fft(descs[big], bases[big], sh, ws=ws)
         fft_tuned = dict(variant=fft_choice, ms_by_variant=[round(t, 4) for t in fft_times])
     else:
-        api.rb_set_fft_variant(d, args.fft_variant)
+        api.rb_set_fft_variant(descs[0], args.fft_variant)
         fft_tuned = dict(variant=args.fft_variant, pinned=True)
+    tuned = []
     if args.precision != "fp32":
-        if args.stage1_variant is None:
-            _, bavg_t = api.rb_basis_filter(d, basis, sh, keep_beta=False, ws=ws)
-            chosen, times = api.rb_tune_stage1(d, basis, bavg_t, ws=ws)
-            tuned = dict(variant=chosen, n_tile=[256, 128][chosen], ms_by_variant=times)
-            del bavg_t
-        else:
-            api.rb_set_stage1_variant(d, args.stage1_variant)
-            tuned = dict(variant=args.stage1_variant, n_tile=[256, 128][args.stage1_variant], pinned=True)
+        for d, b in zip(descs, bases):
+            if args.stage1_variant is None:
+                _, bavg_t = api.rb_basis_filter(d, b, sh, keep_beta=False, ws=ws)
+                chosen, times = api.rb_tune_stage1(d, b, bavg_t, ws=ws)
+                tuned.append(dict(variant=chosen, n_tile=[256, 128][chosen], ms_by_variant=times))
+                del bavg_t
+            else:
+                api.rb_set_stage1_variant(d, args.stage1_variant)
+                tuned.append(dict(variant=args.stage1_variant, pinned=True))
     del sh
     cap = 1 << 23
     trig = torch.empty(cap * 24, dtype=torch.uint8, device="cuda")
 
     def step():
-        return api.rb_filter(d, basis, strain_d, psd_d, capacity=cap, ws=ws, trig=trig)
+        return api.rb_filter_banks(descs, bases, strain_d, psd_d, capacity=cap, ws=ws, trig=trig)
 
     for _ in range(args.warmup):
         step()
@@ -589,43 +708,35 @@ def main():
         dist.barrier()
     rb_trig = api.triggers_numpy(trig, nt)
 
-    # per-stage timing (CUDA events recorded by the library on the launching stream)
+    # per-stage timing (CUDA events recorded by the library on the launching stream): one event set per
+    # sub-bank, so the means times the number of sub-banks are the per-step totals
     api.rb_profile_start()
     for _ in range(args.steps):
         step()
-    stage_ms, _ = api.rb_profile_stop()
+    stage_mean, _ = api.rb_profile_stop()
+    stage_ms = {k_: v * P for k_, v in stage_mean.items()}
 
-    # end to end through the public call: pinned host strain in, triggers out, every step. The trigger
-    # list of step i (two device and two pinned host buffers) is copied to the host on a second stream
-    # while step i+1 runs; the timed region ends when the last copy has landed.
+    # end to end through the public call: one rb_filter_banks call per step takes the pinned host strain to
+    # pinned host triggers (desc.mem tags both as host buffers; the library copies them on the stream)
     host_strain = torch.from_numpy(wl.strain).pin_memory()
-    host_trig = [torch.empty(cap * 24, dtype=torch.uint8).pin_memory() for _ in range(2)]
-    dev_trig = [trig, torch.empty_like(trig)]
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
-    copy_stream = torch.cuda.Stream()
-    dev_in = torch.empty_like(strain_d)
+    cap_h = min(cap, api.rb_banks_plan(descs).host_trig_capacity)
+    host_trig = torch.empty(cap_h * 24, dtype=torch.uint8).pin_memory()
     h2d = host_strain.numel() * 4
     d2h_total = 0
+    api.rb_filter_banks(descs, bases, host_strain, psd_d, capacity=cap_h, ws=ws, trig=host_trig, host=True)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter()
-    for i in range(args.steps):
-        j = i % 2
-        dev_in.copy_(host_strain, non_blocking=True)
-        if i >= 2:
-            torch.cuda.current_stream().wait_event(copied[j])  # buffer j's copy of step i-2 has landed
-        _, n_e = api.rb_filter(d, basis, dev_in, psd_d, capacity=cap, ws=ws, trig=dev_trig[j])
-        copy_stream.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(copy_stream):
-            host_trig[j][: n_e * 24].copy_(dev_trig[j][: n_e * 24], non_blocking=True)
-            copied[j].record(copy_stream)
+    for _ in range(args.steps):
+        _, n_e = api.rb_filter_banks(descs, bases, host_strain, psd_d, capacity=cap_h, ws=ws, trig=host_trig,
+                                     host=True)
         d2h_total += n_e * 24 + 24
     torch.cuda.synchronize()
     e2e_ms, e2e_value = replicas.job_rate(T * secs_per_block, (time.perf_counter() - t_e2e) * 1e3 / args.steps,
                                           dist, "cuda")
 
-    # the template method on the same GPU (comparator) and the accuracy gate against it
+    # the template method on the same GPU (comparator) and the accuracy gate
     plain = None
-    acc = None
+    acc = dict(gate=dict(tol=args.tol, max_template_loss=max(sb["max_loss"] for sb in subs)))
     if not args.no_plain:
         dp = api.make_desc(g.fs, g.n, 1, T, w=args.w, rho_ii=wl.rho_ii)
         wsp = api.workspace(dp)
@@ -642,18 +753,34 @@ def main():
         pms = e0.elapsed_time(e1) / psteps
         plain = dict(ms_per_step=pms, value=world * T * secs_per_block / (pms / 1e3), unit=UNIT,
                      impl="template method, fused Stockham FFT (this library)", speedup=pms / ms)
-        acc = accuracy(rb_trig, api.triggers_numpy(ptrig, npl), args.w, wl.rho_ii)
-        del wsp
-        sh_c = api.rb_whiten(d, strain_d, psd_d, ws=ws)
+        acc["noise_triggers"] = noise_accuracy(rb_trig, api.triggers_numpy(ptrig, npl), args.w, wl.rho_ii)
+        acc["gate"]["recovery"] = acc["noise_triggers"]["recovery"]
+        del wsp, ptrig
+        # injections against the FP64 oracle's template method: the noiseless block isolates the method's
+        # SNR loss (the gate); the noisy block adds the noise in the discarded basis directions
+        wl0 = inputs.full(w=args.w, k=args.k or 256, n_templates=args.templates, n=args.n, segment=rank, noise=False)
+        inj0 = injection_snrs(api, torch, wl0, subs, rows, templates, psd_d, args, 2.0, 3.0, descs_for)
+        inj1 = injection_snrs(api, torch, wl, subs, rows, templates, psd_d, args, rho_i, wl.rho_ii, descs_for)
+        l0 = [x["rel_loss"] for x in inj0 if x.get("rel_loss") is not None]
+        l1 = [x["rel_loss"] for x in inj1 if x.get("rel_loss") is not None]
+        acc["gate"]["noiseless_injection_max_rel_loss"] = max(l0) if l0 else None
+        acc["gate"]["noiseless_injections_found"] = f"{len(l0)} of {len(inj0)}"
+        acc["gate"]["passed"] = bool(acc["gate"]["max_template_loss"] <= args.tol and l0 and max(l0) <= args.tol
+                                     and acc["gate"]["recovery"] >= args.recovery)
+        acc["injections_noiseless"] = inj0
+        acc["injections_noisy"] = dict(max_abs_rel_err=max(abs(x) for x in l1) if l1 else None,
+                                       found=f"{len(l1)} of {len(inj1)}", per_injection=inj1)
+        sh_c = api.rb_whiten(descs[0], strain_d, psd_d, ws=ws)
         cufft = cufft_comparator(torch, templates, sh_c, g.n, args.w, wl.rho_ii, secs_per_block)
         cufft["speedup"] = value / cufft["value"]
         plain["cufft"] = cufft
-        cbf = cufft_basis_filter(torch, basis.vectors, sh_c, g.n, args.w)
+        vec = torch.cat([sb["basis"].vectors for sb in subs])
+        cbf = cufft_basis_filter(torch, vec, sh_c, g.n, args.w)
         cbf["speedup"] = cbf["ms"] / stage_ms["basis_filter"]
         plain["cufft_basis_filter"] = cbf
-        del sh_c
+        del sh_c, vec
 
-    # roofline of the dominant stage
+    # roofline of the dominant stage (totals over the sub-banks)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -663,14 +790,18 @@ def main():
     tensor = peaks.get("bf16_tflops_sustained", 1700.0)
     smmax = peaks.get("sm_max_mhz", 2070.0)
     half, nb = g.n // 2, g.n // (2 * args.w)
-    dom = max(("basis_filter", "first_stage", "second_stage"), key=lambda s: stage_ms[s])
+    ksum = sum(sb["k"] for sb in subs)
+    dom = max(("basis_filter", "first_stage", "second_stage"), key=lambda s_: stage_ms[s_])
     if dom == "second_stage":
         # algorithmic work: k complex MACs for each of the w samples of every candidate (8 flop each)
-        sh_n = api.rb_whiten(d, strain_d, psd_d, ws=ws)
-        _, bavg_n = api.rb_basis_filter(d, basis, sh_n, keep_beta=False, ws=ws)
-        _, n_cand = api.rb_stage1(d, basis, bavg_n, ws=ws)
-        del sh_n, bavg_n
-        flops = 8.0 * args.k * args.w * n_cand
+        flops, n_cand = 0.0, 0
+        for d, sb in zip(descs, subs):
+            sh_n = api.rb_whiten(d, strain_d, psd_d, ws=ws)
+            _, bavg_n = api.rb_basis_filter(d, sb["basis"], sh_n, keep_beta=False, ws=ws)
+            _, nc = api.rb_stage1(d, sb["basis"], bavg_n, ws=ws)
+            flops += 8.0 * sb["k"] * args.w * nc
+            n_cand += nc
+            del sh_n, bavg_n
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
         if args.stage2 == "tc":
             roof = dict(bound="tensor", achieved=achieved, peak=tensor, unit="TFLOP/s", kernel="k_stage2_tc",
@@ -683,23 +814,23 @@ def main():
                         issued_mma_flops_ratio=3.0, candidates=int(n_cand))
             key, srcs = roof["kernel"], ("paper_2110_13115_gb300/csrc/stage2.cu",)
     elif dom == "first_stage":
-        flops = 8.0 * T * args.k * nb
+        flops = sum(8.0 * sb["T"] * sb["k"] * nb for sb in subs)
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
         if args.precision == "fp32":
             peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
             roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", kernel="k_stage1_simt",
                         peak_source="152 SMs x 128 FP32 lanes x 2 flop x max SM clock")
         else:
-            peak = tensor
-            roof = dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", kernel="k_stage1_tc",
+            roof = dict(bound="tensor", achieved=achieved, peak=tensor, unit="TFLOP/s", kernel="k_stage1_tc",
                         peak_source="MEASURED_PEAKS bf16_tflops_sustained (fp16 nominal rate = bf16)",
-                        issued_mma_flops_ratio=3.0 if "split" in args.precision else 1.0)
+                        issued_mma_flops_ratio=3.0 if args.precision in ("fp16_split", "bf16_split") else
+                        (2.0 if args.precision == "fp16_split_a" else 1.0))
         key, srcs = roof["kernel"], ("paper_2110_13115_gb300/csrc/gemm_tc.cu", "paper_2110_13115_gb300/csrc/tma.cuh")
     else:
-        byts = args.k * (half * 8 + half * 8 + nb * 8)
+        byts = ksum * (half * 8 + half * 8 + nb * 8)
         achieved = byts / (stage_ms[dom] / 1e3) / 1e9
         roof = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", kernel="k_pass_a+k_pass_b (basis)",
-                    peak_source="MEASURED_PEAKS hbm_gbs")
+                    peak_source="MEASURED_PEAKS hbm_gbs", algorithmic_bytes=byts)
         key, srcs = "basis_filter", ("paper_2110_13115_gb300/csrc/filter.cu", "paper_2110_13115_gb300/csrc/fft.cuh")
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = traffic_from_profiles(key, source_hash(*srcs))
@@ -715,29 +846,40 @@ def main():
 
     clocks = clk.summary()
     refined = None
+    batch = None
     if rank == 0 and world == 1:  # after every timed region; a failure here only loses this entry
         try:
             refined = refine_rate(api, torch)
         except Exception as exc:  # noqa: BLE001
             refined = dict(error=f"{type(exc).__name__}: {exc}"[:300])
+        if args.batch_segments > 0:
+            del templates, ws, trig, host_trig
+            torch.cuda.empty_cache()
+            try:
+                batch = batch_measure(args, args.batch_segments, steps=3, warmup=3)
+            except Exception as exc:  # noqa: BLE001
+                batch = dict(error=f"{type(exc).__name__}: {exc}"[:300])
     out = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
                data="synthetic",
                config=dict(workload=wl.name, templates=T, block_samples=g.n, fs=g.fs, valid_seconds=secs_per_block,
-                           k=args.k, w=args.w, rho_I=rho_i, rho_II=wl.rho_ii, first_stage=args.precision,
+                           subbanks=[dict(templates=sb["T"], k=sb["k"], max_template_loss=sb["max_loss"],
+                                          eq8_loss=sb["eq8_loss"]) for sb in subs],
+                           k_total=ksum, w=args.w, rho_I=rho_i, rho_II=wl.rho_ii, first_stage=args.precision,
                            rho_I_calibration=f"noise-only block, {n_cal} flat triggers, recovery {args.recovery}",
-                           l2="inputs larger than L2: the basis alone is 537 MB per step",
+                           l2="inputs larger than L2: the bases alone are >= 500 MB per step",
                            first_stage_tile=tuned, fft_schedule=fft_tuned,
                            second_stage={"mma": "mma.sync", "tc": "tcgen05"}[args.stage2],
                            parallelism=f"replicas x{world} (one block per GPU)"),
                roofline=roof, cpu_baseline=cpu,
                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h_total // args.steps,
-                        overlap="the triggers of step i are copied to pinned host memory on a second stream "
-                                "during step i+1 (double-buffered)"),
+                        call="rb_filter_banks with desc.mem = RB_MEM_HOST_STRAIN | RB_MEM_HOST_TRIGGERS (pinned host "
+                             "strain in, pinned host triggers out, copies inside the call)"),
                gpu_launches=int(launches), clocks=clocks, stage_ms=stage_ms, plain_mf=plain, accuracy=acc,
-               basis=dict(build_s=build_s, max_truncation_loss=float(trunc.max()), mean_truncation_loss=float(trunc.mean()),
-                          max_truncation_loss_by_k=loss_by_k, oversample=64, power_iters=1),
-               refine=refined, n_triggers=int(nt))
+               basis=dict(build_s=build_s, tol=args.tol, k_build=args.k_build, oversample=64, power_iters=1,
+                          max_truncation_loss=max(sb["max_loss"] for sb in subs),
+                          mean_truncation_loss=float(np.mean(np.concatenate([sb["template_loss"] for sb in subs])))),
+               refine=refined, batch=batch, n_triggers=int(nt))
     if rank == 0:
         print(json.dumps(out))
     if dist:
