@@ -262,6 +262,38 @@ int rb_filter_banks(const rb_filter_desc* descs, const rb_basis* bases, int32_t 
                     size_t workspace_bytes, void* stream);
 
 /*
+ * rb_stage1_folded - the first stage by the template method instead of the basis (Sec. III.D,
+ * Eqs. 10-12): the bin average of a template's SNR series is one inverse DFT of length M = n / w of
+ * the folded spectrum
+ *   Omega(f') = (1/w) sum_l Q[l M + f'] G(l M + f'),   G(f) = sum_{r<w} exp(2 pi i f r / n),
+ * Q[j] = s_hat[j] conj(g_t[j]) on 0 < j < n/2 (zero above, so only l < w/2 contributes), and
+ *   <z>_b = sum_{f' < M} Omega(f') exp(2 pi i f' b / M),   b in [M/2, M) (the valid bins of Eq. 9).
+ * G is evaluated in closed form, (1 - e^(2 pi i f w / n)) / (1 - e^(2 pi i f / n)) with G(0) = w, in FP64.
+ * Candidates (t, b) with |<z>_b| >= rho_I are written as by rb_stage1 (bin = b), in no set order. The
+ * strain is whitened inside the call (as rb_filter_plain).
+ *   templates: [T][n/2] complex whitened unit-norm templates (g_t / sigma_t, as rb_templates).
+ *   strain: [n] float32.  psd: [n/2 + 1] float64.  desc: fs, n, w (2..16), n_templates, rho_i,
+ *   cand_capacity, block_id used (k, precision, rho_ii ignored; mem must be 0).
+ *   cand: [cand_capacity] output; n_cand (host). workspace: rb_folded_plan size. Synchronises `stream`.
+ *   Errors: RB_ERR_BAD_INPUT (w < 2, NULL array, PSD), RB_ERR_UNSUPPORTED (n / w < 1024),
+ *   RB_ERR_OOM (workspace), RB_ERR_OVERFLOW (more candidates than cand_capacity; *n_cand = count).
+ */
+int rb_folded_plan(const rb_filter_desc* desc, size_t* workspace_bytes /* host */);
+int rb_stage1_folded(const rb_filter_desc* desc, const float* templates, const float* strain, const double* psd,
+                     rb_candidate* cand, int64_t* n_cand, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rb_stage1_lowpass - the low-pass alternative to the first stage that the paper compares with
+ * (Sec. III.G): each template's SNR series low-passed to the lowest M = n / w frequency bins of its
+ * one-sided spectrum and decimated by w,
+ *   z_lp[b] = sum_{j < M} s_hat[j] conj(g_t[j]) exp(2 pi i j b / M),   b in [M/2, M),
+ * one inverse DFT of length M per template, candidates where |z_lp[b]| >= rho_I (bin = b, as
+ * rb_stage1_folded). Same arguments, workspace (rb_folded_plan) and errors as rb_stage1_folded.
+ */
+int rb_stage1_lowpass(const rb_filter_desc* desc, const float* templates, const float* strain, const double* psd,
+                      rb_candidate* cand, int64_t* n_cand, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * rb_filter_plain - the template method (Sec. II, Eq. 4; the baseline of Sec. IV.B.2):
  * per template one inverse FFT of s_hat * conj(h_hat_t), rho = |z| (templates given
  * unit-normalised), per window of w valid samples the arg-max kept when rho >= rho_II.

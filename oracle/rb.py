@@ -21,14 +21,18 @@ Follows arXiv:2110.13115:
   DFT of the folded spectrum Omega(f') = (1/w) sum_l Q[l n/w + f'] G(l n/w + f'),
   G(f) = sum_{r<w} exp(2 pi i f r / n), with the unnormalised inverse DFT of Eq. 6 (Eqs. 10-12 mix
   normalisation conventions; this one makes the folded series equal the bin mean exactly).
+* Sec. III.G: the low-pass alternative to that first stage: the SNR series band-limited to the
+  lowest n/w frequency bins (|f| < fs / (2 w) of the series' one-sided spectrum Q) and decimated by w,
+  z_lp[b] = sum_{j < n/w} Q[j] exp(2 pi i j b w / n), b in [0, n/w).
 
 The basis lives in whitened coordinates g_t[j] = sqrt(4 df / S_j) h_t[j] on
 0 <= j < n/2, in which <a|b> of Eq. (1) is the Euclidean product.
 
 Pinned by: full-rank reconstruction equal to the template method, the exact
 truncation identity for noiseless self-injections and its bank average
-against Eq. (8), the Eckart-Young residual, binning linearity, and the
-folded-first-stage identity (tests/test_oracle_rb.py).
+against Eq. (8), the Eckart-Young residual, binning linearity, the
+folded-first-stage identity, and the low-pass series against a brick-wall
+filter of the full-rate series followed by decimation (tests/test_oracle_rb.py).
 """
 from __future__ import annotations
 
@@ -144,3 +148,18 @@ def folded_first_stage(s_fd, h, psd, n, fs, w):
     m = n // w
     omega = (q * g).reshape(w, m).sum(axis=0) / w
     return np.fft.ifft(omega) * m
+
+
+def lowpass_first_stage(s_fd, h, psd, n, fs, w):
+    """Sec. III.G: the low-pass and decimation first stage of one template.
+
+    Q[j] = 4 df s_j h_j^* / S_j (0 < j < n/2); z_lp[b] = sum_{j < n/w} Q[j] exp(2 pi i j b / (n/w)) for
+    b in [0, n/w): the full-rate series of Eq. 4 with every frequency bin j >= n/w removed, read at
+    samples b w.
+    """
+    df = fs / n
+    m = n // w
+    q = np.zeros(m, dtype=np.complex128)
+    j = np.arange(1, min(m, n // 2))
+    q[j] = 4.0 * df * s_fd[j] * np.conj(h[j]) / np.asarray(psd, dtype=np.float64)[j]
+    return np.fft.ifft(q) * m

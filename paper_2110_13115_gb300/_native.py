@@ -102,6 +102,9 @@ SIGNATURES = {
     "rb_filter_plain": (C.c_int, [_D, _P, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_static": (C.c_int, [_D, _B, _P, _P, _P, C.c_int64, _I64P, _P]),
     "rb_banks_plan": (C.c_int, [_D, C.c_int32, C.POINTER(rb_filter_sizes)]),
+    "rb_folded_plan": (C.c_int, [_D, C.POINTER(C.c_size_t)]),
+    "rb_stage1_folded": (C.c_int, [_D, _P, _P, _P, _P, _I64P, _P, C.c_size_t, _P]),
+    "rb_stage1_lowpass": (C.c_int, [_D, _P, _P, _P, _P, _I64P, _P, C.c_size_t, _P]),
     "rb_filter_banks": (C.c_int, [_D, _B, C.c_int32, _P, _P, _P, C.c_int64, _I64P, _P, C.c_size_t, _P]),
     "rb_basis_max_loss": (C.c_int, [_B, C.POINTER(C.c_double), _P, C.c_size_t, _P]),
     "rb_batch_plan": (C.c_int, [_D, C.c_int32, C.POINTER(C.c_size_t)]),
@@ -141,6 +144,7 @@ HOST_HOOKS = {
     "rbx_stage1_withhold_copies": (C.c_int, [C.c_int]),
     "rbx_set_stage2_tc": (C.c_int, [C.c_int]),
     "rbx_stage2_withhold_copies": (C.c_int, [C.c_int]),
+    "rbx_set_fft_radix32": (C.c_int, [C.c_int]),
 }
 
 _lib = None

@@ -227,6 +227,32 @@ def truncate(basis: Basis, k: int) -> Basis:
                  singular_values=sv)
 
 
+def rb_folded_plan(desc) -> int:
+    """Workspace bytes of rb_stage1_folded / rb_stage1_lowpass."""
+    nbytes = C.c_size_t(0)
+    N.check("rb_folded_plan", _lib().rb_folded_plan(C.byref(desc), C.byref(nbytes)))
+    return nbytes.value
+
+
+def rb_stage1_lowpass(desc, templates: torch.Tensor, strain: torch.Tensor, psd: torch.Tensor, ws=None, cand=None):
+    """The low-pass and decimation first stage (the paper's comparison); as rb_stage1_folded."""
+    return rb_stage1_folded(desc, templates, strain, psd, ws=ws, cand=cand, _entry="rb_stage1_lowpass")
+
+
+def rb_stage1_folded(desc, templates: torch.Tensor, strain: torch.Tensor, psd: torch.Tensor, ws=None, cand=None,
+                     _entry="rb_stage1_folded"):
+    """First stage by the template method (folded spectrum, length n/w inverse transforms); returns
+    (candidate device buffer, count). templates: complex64 [T][n/2] whitened unit-norm rows."""
+    if ws is None:
+        ws = torch.empty(rb_folded_plan(desc), dtype=torch.uint8, device=strain.device)
+    cand = torch.empty(max(desc.cand_capacity, 1) * 16, dtype=torch.uint8, device=strain.device) if cand is None else cand
+    n = C.c_int64(0)
+    rc = getattr(_lib(), _entry)(C.byref(desc), _p(templates), _p(strain), _p(psd), _p(cand), C.byref(n), _p(ws),
+                                 ws.numel(), _stream())
+    N.check(_entry, rc)
+    return cand, n.value
+
+
 def rb_filter_plain(desc, templates: torch.Tensor, strain: torch.Tensor, psd: torch.Tensor, capacity=1 << 20,
                     ws=None, trig=None):
     """Template-method comparator; templates complex64 [T][n/2] unit-norm whitened."""

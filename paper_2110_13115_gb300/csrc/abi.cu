@@ -142,9 +142,13 @@ void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws
   ws->tables.n1_w = (float2*)take(sizeof(float2) * g.n1);
   ws->tables.n2_w = (float2*)take(sizeof(float2) * g.n2);
   ws->tables.fine_w = (float2*)take(sizeof(float2) * g.n2);
+  ws->tables.w2a_w = (float2*)take(sizeof(float2) * w2_entries(g.n2));
+  ws->tables.w2b_w = (float2*)take(sizeof(float2) * w2_entries(g.n1));
   ws->tables.n1 = ws->tables.n1_w;
   ws->tables.n2 = ws->tables.n2_w;
   ws->tables.fine = ws->tables.fine_w;
+  ws->tables.w2a = ws->tables.w2a_w;
+  ws->tables.w2b = ws->tables.w2b_w;
   ws->wt = (float*)take(sizeof(float) * half);
   ws->shat = (float2*)take(sizeof(float2) * half);
   const int64_t nvec = plain ? d.n_templates : d.k;
@@ -228,6 +232,74 @@ int check_basis(const rb_filter_desc& d, const rb_basis* b, bool need_op = false
     return RB_ERR_BAD_INPUT;
   }
   return RB_OK;
+}
+
+// Folded first stage: the whitening FFT of length n and the folded transforms of length M = n / w
+// share the status block; X holds max(vc M, n) points (the whitening uses one n-point vector).
+struct FoldWs {
+  Geometry gn, gm;
+  Workspace wn, wm;
+  float2* gfold = nullptr;
+  size_t total = 0;
+};
+
+int fold_geometry(const rb_filter_desc& d, FoldWs* f) {
+  int rc = make_geometry(d, &f->gn);
+  if (rc) return rc;
+  const int64_t M = d.n / d.w;
+  if (M < (1 << 10)) {
+    set_detail("the folded series has n / w = %lld points; at least 1024 are supported", (long long)M);
+    return RB_ERR_UNSUPPORTED;
+  }
+  const int p = rb_ilog2(M);
+  f->gm = Geometry{};
+  f->gm.n = M;
+  f->gm.n1 = 1 << (p / 2);
+  f->gm.n2 = 1 << (p - p / 2);
+  f->gm.n_bins = M / 2;
+  return RB_OK;
+}
+
+void carve_fold(const rb_filter_desc& d, char* base, FoldWs* f) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* ptr = base ? base + off : nullptr;
+    off += align256(bytes);
+    return ptr;
+  };
+  const Geometry& gn = f->gn;
+  const Geometry& gm = f->gm;
+  char* st = take(256);
+  for (Workspace* w : {&f->wn, &f->wm}) {
+    w->flags = (unsigned*)st;
+    w->cand_count = st ? (unsigned long long*)(st + 8) : nullptr;
+    w->trig_count = st ? (unsigned long long*)(st + 16) : nullptr;
+    w->host_status = (unsigned long long*)st;
+  }
+  auto tables = [&](Workspace* w, const Geometry& g) {
+    w->tables.n1_w = (float2*)take(sizeof(float2) * g.n1);
+    w->tables.n2_w = (float2*)take(sizeof(float2) * g.n2);
+    w->tables.fine_w = (float2*)take(sizeof(float2) * g.n2);
+    w->tables.w2a_w = (float2*)take(sizeof(float2) * w2_entries(g.n2));
+    w->tables.w2b_w = (float2*)take(sizeof(float2) * w2_entries(g.n1));
+    w->tables.n1 = w->tables.n1_w;
+    w->tables.n2 = w->tables.n2_w;
+    w->tables.fine = w->tables.fine_w;
+    w->tables.w2a = w->tables.w2a_w;
+    w->tables.w2b = w->tables.w2b_w;
+  };
+  tables(&f->wn, gn);
+  tables(&f->wm, gm);
+  f->wn.wt = (float*)take(sizeof(float) * gn.n / 2);
+  f->wn.shat = (float2*)take(sizeof(float2) * gn.n / 2);
+  f->wm.shat = f->wn.shat;
+  f->gfold = (float2*)take(sizeof(float2) * gn.n / 2);
+  int64_t vc = (int64_t(96) << 20) / (gm.n * 8);
+  vc = std::max<int64_t>(1, std::min<int64_t>(vc, std::min<int64_t>(d.n_templates, 65535)));
+  f->wm.vc = (int)vc;
+  f->wn.vc = 1;
+  f->wm.X = f->wn.X = (float2*)take(sizeof(float2) * std::max<int64_t>(gm.n * vc, gn.n));
+  f->total = off;
 }
 
 int run_stage1(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
@@ -844,6 +916,78 @@ int rb_filter_banks(const rb_filter_desc* descs, const rb_basis* bases, int32_t 
     return RB_ERR_OVERFLOW;
   }
   return RB_OK;
+}
+
+int rb_folded_plan(const rb_filter_desc* desc, size_t* workspace_bytes) {
+  if (!desc || !workspace_bytes) {
+    set_detail("NULL argument");
+    return RB_ERR_BAD_INPUT;
+  }
+  FoldWs f;
+  int rc = fold_geometry(*desc, &f);
+  if (rc) return rc;
+  if (desc->w < 2) {
+    set_detail("the folded first stage needs w >= 2");
+    return RB_ERR_BAD_INPUT;
+  }
+  carve_fold(*desc, nullptr, &f);
+  *workspace_bytes = f.total;
+  return RB_OK;
+}
+
+static int template_first_stage(const rb_filter_desc* desc, const float* templates, const float* strain,
+                                const double* psd, rb_candidate* cand, int64_t* n_cand, void* workspace,
+                                size_t workspace_bytes, void* stream, bool lowpass) {
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t need = 0;
+  int rc = rb_folded_plan(desc, &need);
+  if (rc) return rc;
+  if (desc->mem != 0) {
+    set_detail("desc->mem = %d: this call takes device pointers", desc->mem);
+    return RB_ERR_BAD_INPUT;
+  }
+  if (!templates || !strain || !psd || !n_cand || (desc->cand_capacity > 0 && !cand)) {
+    set_detail("NULL array");
+    return RB_ERR_BAD_INPUT;
+  }
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) {
+    set_detail("workspace %p of %zu bytes; need %zu bytes, 256-byte aligned", workspace, workspace_bytes, need);
+    return RB_ERR_OOM;
+  }
+  FoldWs f;
+  fold_geometry(*desc, &f);
+  carve_fold(*desc, (char*)workspace, &f);
+  RB_CUDA_TRY(cudaMemsetAsync(f.wn.flags, 0, 256, st));
+  if ((rc = init_tables(f.gn, f.wn, psd, desc->fs, st))) return rc;
+  if ((rc = init_tables(f.gm, f.wm, nullptr, desc->fs, st))) return rc;
+  if ((rc = whiten(f.gn, f.wn, strain, f.wn.shat, st))) return rc;
+  if (!lowpass && (rc = init_gfold(f.gfold, desc->n, desc->w, st))) return rc;
+  if ((rc = folded_stage1(f.gm, f.wm, (const float2*)templates, desc->n_templates, f.wn.shat, desc->w,
+                          desc->rho_i * desc->rho_i, desc->block_id, cand, desc->cand_capacity, f.gfold, st,
+                          lowpass)))
+    return rc;
+  Status s;
+  if ((rc = read_status(f.wn, &s, st))) return rc;
+  if (s.flags & RB_FLAG_BAD_PSD) {
+    set_detail("PSD not finite and positive on 0 < j < n/2");
+    return RB_ERR_BAD_INPUT;
+  }
+  *n_cand = (int64_t)s.cand;
+  if ((int64_t)s.cand > desc->cand_capacity) {
+    set_detail("%llu candidates exceed cand_capacity %lld", s.cand, (long long)desc->cand_capacity);
+    return RB_ERR_OVERFLOW;
+  }
+  return RB_OK;
+}
+
+int rb_stage1_folded(const rb_filter_desc* desc, const float* templates, const float* strain, const double* psd,
+                     rb_candidate* cand, int64_t* n_cand, void* workspace, size_t workspace_bytes, void* stream) {
+  return template_first_stage(desc, templates, strain, psd, cand, n_cand, workspace, workspace_bytes, stream, false);
+}
+
+int rb_stage1_lowpass(const rb_filter_desc* desc, const float* templates, const float* strain, const double* psd,
+                      rb_candidate* cand, int64_t* n_cand, void* workspace, size_t workspace_bytes, void* stream) {
+  return template_first_stage(desc, templates, strain, psd, cand, n_cand, workspace, workspace_bytes, stream, true);
 }
 
 int rb_filter_plain(const rb_filter_desc* desc, const float* templates, const float* strain, const double* psd,

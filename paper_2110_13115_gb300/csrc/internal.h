@@ -26,10 +26,16 @@ struct Tables {
   float2* n1_w = nullptr;    // [n1] exp(2 pi i e / n1)
   float2* n2_w = nullptr;    // [n2] exp(2 pi i e / n2)
   float2* fine_w = nullptr;  // [n2] exp(2 pi i e / n)
+  float2* w2a_w = nullptr;   // [32][n2/32 + 1]: exp(2 pi i j r / n2), stage-2 twiddles of the radix-32 pass A
+  float2* w2b_w = nullptr;   // [32][n1/32 + 1]: exp(2 pi i j r / n1), the same for pass B
   const float2* n1 = nullptr;
   const float2* n2 = nullptr;
   const float2* fine = nullptr;
+  const float2* w2a = nullptr;
+  const float2* w2b = nullptr;
 };
+// float2 entries of a stage-2 twiddle table for a column length L
+inline int64_t w2_entries(int L) { return 32 * (int64_t)(L / 32 + 1); }
 
 // A bucketed candidate: the second stage takes its bin from the work piece, so it keeps only the
 // template row and the block id of the trigger it may become.
@@ -78,10 +84,20 @@ int bank_filter(const Geometry& g, const Workspace& ws, const float2* rows, int6
 int plain_filter(const Geometry& g, const Workspace& ws, const float2* tmpl, int64_t T, const float2* shat,
                  int w, float thr2, int64_t sample_offset, int block_id, rb_trigger* trig, int64_t cap,
                  cudaStream_t st);
+// Whether the radix-32 four-step passes run where they apply (host hook rbx_set_fft_radix32).
+bool fft_radix32_enabled();
 // FFT schedule variants of the basis filter and the template-method comparator (per n and w)
 int set_fft_variant(const Geometry& g, int w, int variant);
 int tune_fft(const Geometry& g, const Workspace& ws, const float2* rows, int64_t nvec, const float2* shat,
              float2* beta, float2* bavg, int w, double* ms, int* chosen, cudaStream_t st);
+// Fast first stage by the template method (Sec. III.D): gfold[j] = G(j) / w on j < n/2, then per template
+// the folded spectrum's inverse transform of length gm.n = n / w, candidates where |<z>_b|^2 >= thr2
+// (counted at wm.cand_count, at most cap stored).
+int init_gfold(float2* gfold, int64_t n, int w, cudaStream_t st);
+// lowpass: the first stage of Sec. III.G instead (the product's lowest n / w bins, no fold).
+int folded_stage1(const Geometry& gm, const Workspace& wm, const float2* tmpl, int64_t T, const float2* shat, int w,
+                  float thr2, int block_id, rb_candidate* cand, int64_t cap, const float2* gfold, cudaStream_t st,
+                  bool lowpass = false);
 int stage1_simt(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
                 const float2* bavg, rb_candidate* cand, cudaStream_t st);
 int pack_beta(const rb_filter_desc& d, const Geometry& g, const float2* bavg, void* hi, void* lo,

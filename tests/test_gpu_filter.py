@@ -371,3 +371,47 @@ def test_stage2_tc_parity(api, w, k):
     ref2 = np.zeros(len(mma), dtype=mf.TRIGGER_DTYPE)
     ref2["template"], ref2["sample"], ref2["snr"], ref2["phase"] = mma["tmpl"], mma["sample"], mma["snr"], mma["phase"]
     compare_triggers(got, ref2, w, rho_ii, ref_rho=zr)
+
+
+@pytest.mark.parametrize("n,w", [(1 << 16, 8), (1 << 17, 16), (1 << 18, 1), (1 << 19, 8), (1 << 20, 16), (1 << 20, 4)])
+def test_radix32_passes_vs_radix16_and_oracle(api, n, w):
+    """The radix-32 four-step passes (every n >= 2^16) against the radix-16 passes and the FP64 oracle:
+    basis series, bin means and template-method triggers."""
+    from paper_2110_13115_gb300 import _native as N
+
+    k, T = 6, 5
+    g, psd, x = _strain(n, fs=2048.0, seed=6)
+    half = n // 2
+    P = inputs.unit_rows(k, half, seed=61).astype(np.complex64)
+    d = api.make_desc(g.fs, n, k, 1, w=w)
+    basis = api.Basis(_dev(P), _dev(np.ones((1, k), np.complex64)), n)
+    ws = api.workspace(d)
+    sh = api.rb_whiten(d, _dev(x), _dev(psd), ws=ws)
+    out = {}
+    try:
+        for r32 in (4, 3, 2, 1, 0):  # radix-32 variants 3..0, then the radix-16 passes
+            N.load().rbx_set_fft_radix32(r32)
+            beta, bavg = api.rb_basis_filter(d, basis, sh, ws=ws)
+            out[r32] = (beta.cpu().numpy(), bavg.cpu().numpy())
+    finally:
+        N.load().rbx_set_fft_radix32(4)
+    s_fd = mf.strain_fd(x.astype(np.float64), g.fs)
+    ref = rb.basis_series(s_fd, psd, P.astype(np.complex128), n, g.fs)
+    rref = ref[:, half:]
+    scale = np.sqrt(np.mean(np.abs(rref) ** 2))
+    aref = rb.bin_average(ref, w)[:, n // (2 * w):]
+    for r32, (beta, bavg) in out.items():
+        assert np.abs(beta - rref).max() / scale < 3e-5, r32
+        assert np.abs(bavg - aref).max() / scale < 3e-5, r32
+    assert np.abs(out[4][0] - out[0][0]).max() / scale < 3e-5
+    # the staged stores change no arithmetic: variants with and without them agree bit for bit
+    assert np.array_equal(out[4][0], out[2][0]) and np.array_equal(out[3][0], out[1][0])
+    # the template method through the same passes (rows as unit-norm templates)
+    rho_ii = 3.0
+    dp = api.make_desc(g.fs, n, 1, k, w=w, rho_ii=rho_ii)
+    buf, nt = api.rb_filter_plain(dp, _dev(P), _dev(x), _dev(psd))
+    got = api.triggers_numpy(buf, nt)
+    rho = np.abs(ref)
+    tref = np.concatenate([mf.window_triggers(t, rho[t], ref[t], n, w, rho_ii) for t in range(k)])
+    stats = compare_triggers(got, tref, w, rho_ii, ref_rho=rho[:, half:])
+    assert stats["both"] > 5, stats

@@ -100,3 +100,20 @@ def test_folded_first_stage_identity(small, w):
     z, sig = mf.snr_series(sd, hs[4], psd, g.n, g.fs)
     zb = rb.folded_first_stage(sd, hs[4], psd, g.n, g.fs, w)
     np.testing.assert_allclose(zb, z.reshape(-1, w).mean(axis=1), atol=1e-11 * np.abs(z).max())
+
+
+@pytest.mark.parametrize("w", [2, 4, 8, 16])
+def test_lowpass_first_stage_is_band_limited_decimated_series(small, w):
+    """Sec. III.G: the low-pass first stage equals the template method's full-rate series of a template
+    band-limited to the lowest n/w frequency bins, read every w samples."""
+    g, psd, bank, hs, ghat, sigma = small
+    strain = inputs.coloured_noise(g, psd, 11)
+    sd = mf.strain_fd(strain, g.fs)
+    h = hs[3].copy()
+    h[g.n // w:] = 0.0
+    z, _ = mf.snr_series(sd, h, psd, g.n, g.fs)
+    zl = rb.lowpass_first_stage(sd, hs[3], psd, g.n, g.fs, w)
+    np.testing.assert_allclose(zl, z[::w], atol=1e-11 * np.abs(z).max())
+    # and it differs from the bin average, which keeps every frequency (Eq. 11)
+    zb = rb.folded_first_stage(sd, hs[3], psd, g.n, g.fs, w)
+    assert np.abs(zl - zb).max() > 1e-3 * np.abs(zb).max()
