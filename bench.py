@@ -215,8 +215,9 @@ def source_hash(*paths):
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles(kernel_key, src_hash):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current source."""
+def traffic_from_profiles(kernel_key, src_hash, units=None):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current source; a summary
+    taken on a smaller case gives bytes per unit (basis vector), scaled here by the units of a launch."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -226,6 +227,8 @@ def traffic_from_profiles(kernel_key, src_hash):
         return None
     if not d or d.get("source_hash") != src_hash:
         return None
+    if "dram_bytes_per_unit" in d and units:
+        return d["dram_bytes_per_unit"] * units
     return d.get("dram_bytes_per_launch")
 
 
@@ -801,6 +804,14 @@ def run_sweep(args):
     p_t = sum(sb["T"] * sb["k"] for sb in subs) / T
     z_basic = n * T * (5 * math.log2(n) + 6)
     strain = torch.from_numpy(blocks[0]).cuda()
+    # the FFT schedule tuned for every w (shared by the template method and the basis filter), as the
+    # headline run does
+    for w in (2, 4, 8, 16):
+        sb = max(subs, key=lambda x: x["k"])
+        dt_ = api.make_desc(g.fs, g.n, sb["k"], sb["T"], w=w)
+        wst = api.workspace(dt_)
+        api.rb_tune_fft(dt_, sb["basis"], api.rb_whiten(dt_, strain, psd_d, ws=wst), ws=wst)
+        del wst
     dp = api.make_desc(g.fs, g.n, 1, T, w=8, rho_ii=5.0)
     api.rb_filter_plain(dp, templates, strain, psd_d, capacity=1 << 24)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -833,6 +844,12 @@ def run_sweep(args):
                                    cand_capacity=1 << 25) for sb in subs]
             for d_, sb in zip(descs, subs):
                 api.rb_pack_coeff(d_, sb["basis"])
+            sh_t = api.rb_whiten(descs[0], strain, psd_d)
+            for d_, sb in zip(descs, subs):  # first-stage tile per sub-bank, as the headline run does
+                _, bavg_t = api.rb_basis_filter(d_, sb["basis"], sh_t, keep_beta=False)
+                api.rb_tune_stage1(d_, sb["basis"], bavg_t)
+                del bavg_t
+            del sh_t
             ws = api.banks_workspace(descs)
             for _ in range(3):
                 api.rb_filter_banks(descs, [sb["basis"] for sb in subs], strain, psd_d, capacity=1 << 23, ws=ws)
@@ -1117,9 +1134,10 @@ def main():
         achieved = byts / (stage_ms[dom] / 1e3) / 1e9
         roof = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", kernel="k_pass_a+k_pass_b (basis)",
                     peak_source="MEASURED_PEAKS hbm_gbs", algorithmic_bytes=byts)
-        key, srcs = "basis_filter", ("paper_2110_13115_gb300/csrc/filter.cu", "paper_2110_13115_gb300/csrc/fft.cuh")
+        key, srcs = "basis_filter", ("paper_2110_13115_gb300/csrc/filter.cu", "paper_2110_13115_gb300/csrc/fft.cuh",
+                                     "paper_2110_13115_gb300/csrc/fft2.cuh")
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = traffic_from_profiles(key, source_hash(*srcs))
+    roof["traffic"] = traffic_from_profiles(key, source_hash(*srcs), units=ksum if key == "basis_filter" else None)
     roof["stage"] = dom
 
     cpu = None
