@@ -37,12 +37,15 @@ struct Tables {
 // float2 entries of a stage-2 twiddle table for a column length L
 inline int64_t w2_entries(int L) { return 32 * (int64_t)(L / 32 + 1); }
 
-// A bucketed candidate: the second stage takes its bin from the work piece, so it keeps only the
-// template row and the block id of the trigger it may become.
-struct alignas(8) SortedCand {
+// A bucketed second-stage record: the template row and block id of a run of candidates in one
+// group of bins, and the mask of those bins within the group (bit j: bin j of the group); the group
+// comes with the work piece.
+struct SortedCand {
   int tmpl;
   int block;
+  unsigned mask;
 };
+
 
 // Carving of the caller's workspace (all offsets 256-byte aligned).
 struct Workspace {
@@ -119,7 +122,14 @@ int stage2_tc_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g,
                   const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st,
                   int tmpl_base = 0);
 bool stage2_use_tc();
-// The two halves of stage2_bucketed: bucketing of ws.cand by bin, then the reconstruction.
+int stage2_tc_mode();  // 0 off, 1 automatic group width, 16 or 32 samples per group
+// Samples per bin group of the tcgen05 second stage for desc (16 or 32), 0 when it cannot run it
+// (w > 8, or no room for a coefficient ring beside the windows).
+int stage2_tc_samples(const rb_filter_desc& d);
+// Bins per group for desc: stage2_tc_samples / w for the tcgen05 second stage, 1 for the mma.sync
+// one; the bucketing and the reconstruction of one call see the same value.
+int stage2_group(const rb_filter_desc& d);
+// The two halves of stage2_bucketed: bucketing of ws.cand by bin group, then the reconstruction.
 int stage2_bucket(const rb_filter_desc& d, const Geometry& g, const Workspace& ws, int bin_lo, cudaStream_t st);
 // tmpl_base is added to every trigger's template row (sub-banks filtered into one list).
 int stage2_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,

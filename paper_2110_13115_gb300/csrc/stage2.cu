@@ -1,9 +1,13 @@
 // Second stage of the hierarchy (arXiv:2110.13115 Sec. III.C, full-resolution reconstruction of
 // every sample inside the triggering bins; Sec. III.E custom kernel), grouped by bin.
 //
-// 1. First-stage candidates are bucketed by bin: per-bin counts and a scatter, both through
-//    per-chunk shared-memory histograms, around an exclusive scan; the bucketed copy holds
-//    8-byte (template, block) records, the bin coming with the work piece.
+// 1. First-stage candidates are bucketed by groups of G consecutive bins (G = 1 for this kernel, more
+//    for the tcgen05 one): per-group counts and a scatter, both through per-chunk shared-memory
+//    histograms, around an exclusive scan. A run of candidates of one template and block in strictly
+//    increasing bins of one group (the first stage writes a template's hits of a 32-bin chunk
+//    consecutively, in bin order) becomes one record (template, block, mask of its bins in the
+//    group), so its coefficient row is gathered once for all of them; the group comes with the work
+//    piece.
 // 2. The scan cuts each non-empty bin into pieces of at most kStage2Piece candidates, so a bin
 //    with thousands of candidates is shared by many CTAs and empty bins cost nothing. For each
 //    piece a CTA stages the bin's k x w window of beta (unless it already holds that bin) as
@@ -30,6 +34,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kPiece = rb::kStage2Piece;  // candidates per second-stage work item
+std::atomic<int> g_stage2_ring{2};  // coefficient ring slots of the mma.sync second stage (0: registers)
 
 // Bucketing works on chunks of consecutive candidates. The first stage emits candidates in tile
 // order and the tiles in flight share their bins, so a chunk's bins lie in a narrow range: each CTA
@@ -48,12 +53,28 @@ __device__ __forceinline__ int block_min(int v, int* red) {  // blockDim.x == 25
   return m;
 }
 
-// Per-bin counts of the candidates [0, min(cap, count)) whose bin (relative to bin0) lies in
-// [blo, nb): bins before blo are dropped, as a block whose earlier valid samples another block
-// already covers keeps only [blo, nb). 256 threads, chunks of 4096 candidates.
+// Whether candidate c continues the run of its predecessor p: p kept (its bin relative to bin0 in
+// [blo, nb)), c's bin in range, the same template and block, the same group of 2^gs bins, and a
+// strictly later bin. A run therefore holds at most 2^gs candidates, and with gs = 0 every kept
+// candidate starts its own.
+__device__ __forceinline__ bool continues_run(const rb_candidate& p, const rb_candidate& c, int bin0, int blo, int nb,
+                                              int gs) {
+  const int px = p.bin - bin0, cx = c.bin - bin0;
+  return px >= blo && px < cx && cx < nb && p.tmpl == c.tmpl && p.block == c.block && (px >> gs) == (cx >> gs);
+}
+
+// Whether candidate i (kept) starts a run: one record per run (every candidate when gs = 0).
+__device__ __forceinline__ bool run_head(const rb_candidate* __restrict__ cand, int64_t i, const rb_candidate& c,
+                                         int bin0, int blo, int nb, int gs) {
+  return gs == 0 || i == 0 || !continues_run(cand[i - 1], c, bin0, blo, nb, gs);
+}
+
+// Per-group record counts (groups of 2^gs bins) of the candidates [0, min(cap, count)) whose bin
+// (relative to bin0) lies in [blo, nb): bins before blo are dropped, as a block whose earlier valid
+// samples another block already covers keeps only [blo, nb). 256 threads, chunks of 4096 candidates.
 __global__ void __launch_bounds__(256) k_bin_count(const rb_candidate* __restrict__ cand,
                                                    const unsigned long long* dev_count, int64_t cap, int bin0,
-                                                   int blo, int nb, unsigned* __restrict__ count) {
+                                                   int blo, int nb, int gs, unsigned* __restrict__ count) {
   constexpr int PER = 16, CHUNK = 256 * PER;
   __shared__ unsigned hist[kWin];
   __shared__ int red[8];
@@ -67,8 +88,9 @@ __global__ void __launch_bounds__(256) k_bin_count(const rb_candidate* __restric
       const int64_t i = c0 + j * 256 + tid;
       b[j] = -1;
       if (i < n) {
-        const int x = cand[i].bin - bin0;
-        if (x >= blo && x < nb) b[j] = x;
+        const rb_candidate c = cand[i];
+        const int x = c.bin - bin0;
+        if (x >= blo && x < nb && run_head(cand, i, c, bin0, blo, nb, gs)) b[j] = x >> gs;
       }
       if (b[j] >= 0) mn = min(mn, b[j]);
     }
@@ -208,12 +230,13 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
   }
 }
 
-// Candidates into bin order, by chunks of 2048 (256 threads): a candidate's rank among the chunk's
-// candidates of its bin comes from a shared-memory atomic, the chunk's base in the bin from one
-// global cursor atomic per (chunk, bin); bins outside the window take one global atomic each.
+// Records into group order, by chunks of 2048 candidates (256 threads): each run head gathers its
+// run's bin mask (at most 2^gs following candidates); a record's rank among the chunk's records of
+// its group comes from a shared-memory atomic, the chunk's base in the group from one global cursor
+// atomic per (chunk, group); groups outside the window take one global atomic each.
 __global__ void __launch_bounds__(256) k_bin_scatter(const rb_candidate* __restrict__ cand,
                                                      const unsigned long long* dev_count, int64_t cap, int bin0,
-                                                     int blo, int nb, const unsigned* __restrict__ start,
+                                                     int blo, int nb, int gs, const unsigned* __restrict__ start,
                                                      unsigned* __restrict__ cursor,
                                                      rb::SortedCand* __restrict__ out) {
   constexpr int PER = 8, CHUNK = 256 * PER;
@@ -232,7 +255,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const rb_candidate* __restr
       if (i < n) {
         c[j] = cand[i];
         const int x = c[j].bin - bin0;
-        if (x >= blo && x < nb) b[j] = x;
+        if (x >= blo && x < nb && run_head(cand, i, c[j], bin0, blo, nb, gs)) b[j] = x >> gs;
       }
       if (b[j] >= 0) mn = min(mn, b[j]);
     }
@@ -258,7 +281,17 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const rb_candidate* __restr
       if (b[j] < 0) continue;
       const int d = b[j] - lo;
       const unsigned pos = d < kWin ? hist[d] + r[j] : atomicAdd(cursor + b[j], 1u);
-      out[start[b[j]] + pos] = rb::SortedCand{c[j].tmpl, c[j].block};
+      const int64_t i = c0 + j * 256 + tid;
+      const int gmask = (1 << gs) - 1;
+      unsigned mask = 1u << ((c[j].bin - bin0) & gmask);
+      rb_candidate prev = c[j];
+      for (int r = 1; r < (1 << gs) && i + r < n; ++r) {
+        const rb_candidate q = cand[i + r];
+        if (!continues_run(prev, q, bin0, blo, nb, gs)) break;
+        mask |= 1u << ((q.bin - bin0) & gmask);
+        prev = q;
+      }
+      out[start[b[j]] + pos] = rb::SortedCand{c[j].tmpl, c[j].block, mask};
     }
     __syncthreads();  // hist and red are reused by the next chunk
   }
@@ -275,8 +308,8 @@ __device__ __forceinline__ void split_h(float x, __half& h, __half& l) {
 
 __device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+  // no side effects: the compiler may interleave independent products
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
@@ -323,8 +356,34 @@ __device__ __forceinline__ void stage_window(const float2* __restrict__ beta, in
   __syncthreads();
 }
 
-// Shared memory per bin: window [W][k16 + 1] float2, then fragments frag[plane][kc][nt][lane] (uint2).
-template <int W>
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gmem), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared-memory bytes of k_stage2_bins<W, D>: fragments frag[plane][kc][nt][lane] (uint2), then one
+// region that holds the bin's window [W][k16 + 1] float2 while it is staged and, while candidates
+// are reconstructed, each warp's ring of D coefficient slots [slot][4][lane] (uint4).
+template <int W, int D>
+constexpr size_t bins_smem(int k16) {
+  const size_t fr = sizeof(uint2) * 2 * (2 * k16 / 16) * S2<W>::NT * 32;
+  const size_t wn = sizeof(float2) * W * (k16 + 1), ring = sizeof(uint4) * 8 * D * 4 * 32;
+  return fr + (wn > ring ? wn : ring);
+}
+
+// D = 0: each lane loads its coefficient fragments into registers (two K-chunk pairs unrolled);
+// D > 0: each lane streams them through a private ring of D slots in shared memory with cp.async,
+// D - 1 K-chunk pairs ahead of the products, so that the gathers of a tile overlap its products
+// without holding registers. A lane reads back only what it copied itself, so its own
+// cp.async.wait_group orders each slot's fill before its reads, and its reads (consumed by the
+// products before the next copy is issued) before the slot's refill.
+template <int W, int D>
 __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict__ ahi, const __half* __restrict__ alo,
                                                      const float2* __restrict__ beta, int k, int k16, int T,
                                                      int64_t half, int bin0, const int4* __restrict__ pieces,
@@ -335,9 +394,11 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
   constexpr int NT = S2<W>::NT;
   extern __shared__ __align__(16) uint8_t s2mem[];
   const int pitch = k16 + 1;                        // padded window rows (bank spread)
-  float2* win = reinterpret_cast<float2*>(s2mem);  // [W][pitch]
   const int nkc = 2 * k16 / 16;                     // K chunks: Re half then Im half (even)
-  uint2* frag = reinterpret_cast<uint2*>(s2mem + sizeof(float2) * W * pitch);  // [2][nkc][NT][32]
+  uint2* frag = reinterpret_cast<uint2*>(s2mem);    // [2][nkc][NT][32]
+  uint8_t* region = s2mem + sizeof(uint2) * 2 * nkc * NT * 32;
+  float2* win = reinterpret_cast<float2*>(region);  // [W][pitch] while a bin is staged
+  uint4* ring = reinterpret_cast<uint4*>(region) + (threadIdx.x >> 5) * (D * 4 * 32);  // this warp's slots
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int g = lane >> 2, t4 = lane & 3;
   const unsigned npieces = *piece_total;
@@ -372,10 +433,39 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
       const uint4* rl1 = reinterpret_cast<const uint4*>(alo + (int64_t)max(tr[1], 0) * p2) + t4;
       const bool v0 = tr[0] >= 0, v1 = tr[1] >= 0;
       const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+      const int nq = nkc / 2;
+      auto issue = [&](int q) {  // K-chunk pair q into slot q % D (zero-filled for an empty row)
+        uint4* sl = ring + (q % (D > 0 ? D : 1)) * 4 * 32 + lane;
+        cp_async16(sl + 0 * 32, rh0 + 4 * q, v0);
+        cp_async16(sl + 1 * 32, rh1 + 4 * q, v1);
+        cp_async16(sl + 2 * 32, rl0 + 4 * q, v0);
+        cp_async16(sl + 3 * 32, rl1 + 4 * q, v1);
+      };
+      if constexpr (D > 0) {
+#pragma unroll
+        for (int s = 0; s < D - 1; ++s) {
+          if (s < nq) issue(s);
+          cp_async_commit();
+        }
+      }
 #pragma unroll 2
-      for (int q = 0; q < nkc / 2; ++q) {
-        const uint4 h0 = v0 ? __ldg(rh0 + 4 * q) : z4, h1 = v1 ? __ldg(rh1 + 4 * q) : z4;
-        const uint4 l0 = v0 ? __ldg(rl0 + 4 * q) : z4, l1 = v1 ? __ldg(rl1 + 4 * q) : z4;
+      for (int q = 0; q < nq; ++q) {
+        uint4 h0, h1, l0, l1;
+        if constexpr (D > 0) {
+          if (q + D - 1 < nq) issue(q + D - 1);
+          cp_async_commit();
+          cp_async_wait<D - 1>();  // the group of pair q is complete
+          const uint4* sl = ring + (q % D) * 4 * 32 + lane;
+          h0 = sl[0 * 32];
+          h1 = sl[1 * 32];
+          l0 = sl[2 * 32];
+          l1 = sl[3 * 32];
+        } else {
+          h0 = v0 ? __ldg(rh0 + 4 * q) : z4;
+          h1 = v1 ? __ldg(rh1 + 4 * q) : z4;
+          l0 = v0 ? __ldg(rl0 + 4 * q) : z4;
+          l1 = v1 ? __ldg(rl1 + 4 * q) : z4;
+        }
 #pragma unroll
         for (int half_q = 0; half_q < 2; ++half_q) {
           const int kc = 2 * q + half_q;
@@ -383,14 +473,19 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
           const uint32_t ah1 = half_q ? h1.z : h1.x, ah3 = half_q ? h1.w : h1.y;
           const uint32_t al0 = half_q ? l0.z : l0.x, al2 = half_q ? l0.w : l0.y;
           const uint32_t al1 = half_q ? l1.z : l1.x, al3 = half_q ? l1.w : l1.y;
+          // the three products of every n-tile, ordered so that consecutive ones are independent
+          uint2 bh[NT], bl[NT];
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt) {
-            const uint2 bh = frag[((0 * nkc + kc) * NT + nt) * 32 + lane];
-            const uint2 bl = frag[((1 * nkc + kc) * NT + nt) * 32 + lane];
-            mma16816(d[nt], ah0, ah1, ah2, ah3, bh.x, bh.y);
-            mma16816(d[nt], ah0, ah1, ah2, ah3, bl.x, bl.y);
-            mma16816(d[nt], al0, al1, al2, al3, bh.x, bh.y);
+            bh[nt] = frag[((0 * nkc + kc) * NT + nt) * 32 + lane];
+            bl[nt] = frag[((1 * nkc + kc) * NT + nt) * 32 + lane];
           }
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) mma16816(d[nt], ah0, ah1, ah2, ah3, bh[nt].x, bh[nt].y);
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) mma16816(d[nt], ah0, ah1, ah2, ah3, bl[nt].x, bl[nt].y);
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) mma16816(d[nt], al0, al1, al2, al3, bh[nt].x, bh[nt].y);
         }
       }
       // thread (g, t) holds, per n-tile, (Re, Im) of sample r = 4 nt + t for rows g and g + 8
@@ -449,20 +544,18 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
   }
 }
 
-template <int W>
+template <int W, int D>
 int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
                 const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, int tmpl_base,
                 cudaStream_t st) {
-  constexpr int NT = S2<W>::NT;
   const int nb = (int)g.n_bins;
   const int k16 = (d.k + 15) / 16 * 16;
-  const int nkc = 2 * k16 / 16;
-  const int smem = (int)(sizeof(float2) * W * (k16 + 1) + sizeof(uint2) * 2 * nkc * NT * 32);
+  const int smem = (int)bins_smem<W, D>(k16);
   if (smem > 200 * 1024) {
     rb::set_detail("k * w too large for the second-stage window (%d x %d)", d.k, W);
     return RB_ERR_UNSUPPORTED;
   }
-  auto kern = k_stage2_bins<W>;
+  auto kern = k_stage2_bins<W, D>;
   if (smem > 48 * 1024) RB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int grid = 152 * 8;
   const __half* ahi = reinterpret_cast<const __half*>(b.coeff_op);
@@ -477,17 +570,26 @@ int launch_bins(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& 
 
 namespace rb {
 
+int stage2_group(const rb_filter_desc& d) {
+  const int samples = stage2_use_tc() ? stage2_tc_samples(d) : 0;
+  return samples > 0 ? samples / d.w : 1;
+}
+
 int stage2_bucket(const rb_filter_desc& d, const Geometry& g, const Workspace& ws, int bin_lo, cudaStream_t st) {
   const int nb = (int)g.n_bins;
   const int bin0 = nb;  // valid bins are [n/(2w), n/w)
-  RB_CUDA_TRY(cudaMemsetAsync(ws.bin_count, 0, sizeof(unsigned) * (nb + 1), st));
-  k_bin_count<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, ws.bin_count);
+  const int G = stage2_group(d);
+  const int gs = __builtin_ctz((unsigned)G);
+  const int ng = (nb + G - 1) / G;
+  RB_CUDA_TRY(cudaMemsetAsync(ws.bin_count, 0, sizeof(unsigned) * (ng + 1), st));
+  k_bin_count<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, gs,
+                                       ws.bin_count);
   RB_LAUNCH_CHECK();
-  k_bin_scan<<<1, 1024, 0, st>>>(ws.bin_count, ws.bin_start, nb, ws.pieces, ws.piece_total, ws.cand_count,
+  k_bin_scan<<<1, 1024, 0, st>>>(ws.bin_count, ws.bin_start, ng, ws.pieces, ws.piece_total, ws.cand_count,
                                  d.cand_capacity, ws.flags);
   RB_LAUNCH_CHECK();
-  k_bin_scatter<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, ws.bin_start,
-                                         ws.bin_count, ws.cand_sorted);
+  k_bin_scatter<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, gs,
+                                         ws.bin_start, ws.bin_count, ws.cand_sorted);
   RB_LAUNCH_CHECK();
   return RB_OK;
 }
@@ -495,16 +597,19 @@ int stage2_bucket(const rb_filter_desc& d, const Geometry& g, const Workspace& w
 int stage2_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g, const Workspace& ws,
                const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st,
                int tmpl_base) {
-  if (stage2_use_tc() && d.w <= 8) {
-    const int rc = stage2_tc_run(d, b, g, ws, beta, trig, cap, counter, st, tmpl_base);
-    if (rc != RB_ERR_UNSUPPORTED) return rc;
-  }
-  switch (d.w) {
-    case 1: return launch_bins<1>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
-    case 2: return launch_bins<2>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
-    case 4: return launch_bins<4>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
-    case 8: return launch_bins<8>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
-    case 16: return launch_bins<16>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
+  if (stage2_group(d) > 1) return stage2_tc_run(d, b, g, ws, beta, trig, cap, counter, st, tmpl_base);
+  const int D = g_stage2_ring.load();
+#define RB_BINS(W_, D_) \
+  if (d.w == W_ && D == D_) return launch_bins<W_, D_>(d, b, g, ws, beta, trig, cap, counter, tmpl_base, st);
+  RB_BINS(1, 0) RB_BINS(1, 2) RB_BINS(1, 3)
+  RB_BINS(2, 0) RB_BINS(2, 2) RB_BINS(2, 3)
+  RB_BINS(4, 0) RB_BINS(4, 2) RB_BINS(4, 3)
+  RB_BINS(8, 0) RB_BINS(8, 2) RB_BINS(8, 3) RB_BINS(8, 4)
+  RB_BINS(16, 0) RB_BINS(16, 2) RB_BINS(16, 3)
+#undef RB_BINS
+  if (d.w == 1 || d.w == 2 || d.w == 4 || d.w == 8 || d.w == 16) {
+    set_detail("no second-stage kernel for w = %d with a ring of %d slots", d.w, D);
+    return RB_ERR_UNSUPPORTED;
   }
   return RB_ERR_BAD_INPUT;
 }
@@ -520,18 +625,31 @@ int stage2_bucketed(const rb_filter_desc& d, const rb_basis& b, const Geometry& 
 }  // namespace rb
 
 namespace {
-std::atomic<int> g_stage2_tc{0};
+std::atomic<int> g_stage2_tc{1};
+}
+
+// Host-only hook (not part of the C ABI): slots of the mma.sync second stage's per-lane coefficient
+// ring (0: loads into registers; 2, the default, and 3 for every w, also 4 for w = 8).
+// RB_ERR_BAD_INPUT otherwise.
+extern "C" int rbx_set_stage2_ring(int slots) {
+  if (slots != 0 && slots != 2 && slots != 3 && slots != 4) return RB_ERR_BAD_INPUT;
+  g_stage2_ring.store(slots);
+  return 0;
 }
 
 namespace rb {
 bool stage2_use_tc() { return g_stage2_tc.load() != 0; }
+int stage2_tc_mode() { return g_stage2_tc.load(); }
 }  // namespace rb
 
-// Host-only hook (not part of the C ABI): 1 selects the tcgen05 second stage (stage2_tc.cu) where it
-// applies (w <= 8 and the window fits shared memory); 0, the default, keeps the per-candidate
-// mma.sync kernel above, which is the faster of the two on the 10,000-template, 2^19-sample workload
-// (1.00 ms against 1.13 ms for its 3.5 M candidates).
-extern "C" int rbx_set_stage2_tc(int on) {
-  g_stage2_tc.store(on ? 1 : 0);
+// Host-only hook (not part of the C ABI): the second-stage kernel. 1 (the default): the tcgen05
+// kernel (stage2_tc.cu) over bin groups of the automatic width, 16 or 32: of that many samples,
+// where it applies (w <= 8 and a coefficient ring fits beside the windows; the mma.sync kernel
+// otherwise); 0: the per-bin mma.sync kernel above. RB_ERR_BAD_INPUT for another value. On the
+// 10,000-template, 2^19-sample workload (3.5 M candidates, 1.9 M records in 16-sample groups) the
+// second stage takes 0.62 ms on tcgen05, 0.70 ms on mma.sync.
+extern "C" int rbx_set_stage2_tc(int mode) {
+  if (mode != 0 && mode != 1 && mode != 16 && mode != 32) return RB_ERR_BAD_INPUT;
+  g_stage2_tc.store(mode);
   return 0;
 }

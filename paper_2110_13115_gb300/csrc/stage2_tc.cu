@@ -1,6 +1,7 @@
 // Second stage on tcgen05 tensor cores (arXiv:2110.13115 Sec. III.C second stage, Sec. III.E custom
-// kernel): for the candidates of one bin, z_t[m] = sum_k conj(a_tk) beta_k[m] over the bin's w
-// samples as one real contraction D[128 candidates][2N] = A[128][K] . B[K][2N] with
+// kernel): for the records of one group of G = 16 / w bins (a record: one template's candidate bins
+// within the group, as a bin mask), z_t[m] = sum_k conj(a_tk) beta_k[m] over the group's S = 16
+// samples as one real contraction D[128 records][2N] = A[128][K] . B[K][2N] (N = 2S) with
 //   A row  = [Re a_t | Im a_t] (K = 2 k16, FP16 hi and lo planes from rb_pack_coeff, in its column order)
 //   B[kk][2r] = Re beta_kk[r] / Im beta_(kk-k16)[r],  B[kk][2r+1] = Im beta_kk[r] / -Re beta_(kk-k16)[r]
 // (the first / second half of K) in FP16 hi (columns 0..N-1) and lo (columns N..2N-1), so
@@ -8,7 +9,10 @@
 // Two products per K step, A_hi . [B_hi | B_lo] and A_lo . [B_hi | B_lo], with FP32 accumulation in
 // tensor memory: the split terms hi.hi + hi.lo + lo.hi (+ lo.lo), FP32-accurate.
 //
-// Persistent kernel, one CTA per SM, 416 threads, over the pieces (<= 512 candidates of one bin)
+// The arg-max over each bin of a record's mask is reported when |z| >= rho_II. Reading a coefficient
+// row once for all of a template's candidate bins of the group cuts the gathers, which bound this
+// kernel, by the number of candidates per record (about 1.8 on clustered candidates at w = 8).
+// Persistent kernel, one CTA per SM, 416 threads, over the pieces (<= 512 records of one group)
 // that the bucketing produced:
 //   warps 0-3  : coefficient producers. Per tile of 128 candidates each warp gathers the coefficient
 //                rows of its 32 candidates, K block by K block, with cp.async into an S-deep ring
@@ -17,17 +21,16 @@
 //                The template index of the next tile and the record of the next piece are loaded
 //                one tile ahead.
 //   warp 4     : tensor-memory allocation and the MMA issuer (one thread), two tiles in flight.
-//   warps 5-8  : epilogue: one tensor-memory lane quarter each; arg-max over the bin, rho_II, triggers.
-//   warps 9-12 : window producers: the bin's B operand (hi and lo windows side by side, 128-byte
+//   warps 5-8  : epilogue: one tensor-memory lane quarter each; arg-max over each bin of the record's
+//                mask, rho_II, triggers.
+//   warps 9-12 : window producers: the group's B operand (hi and lo windows side by side, 128-byte
 //                swizzled K-major), double-buffered, so a piece's window is built while the one before runs.
 // Every mbarrier wait is bounded (1 s); a timeout sets RB_FLAG_TIMEOUT and every role stops; copies
 // and products in flight are waited for (bounded) and tensor memory is freed before the CTA exits.
 //
-// Cost: an M = 128, N = 32, K = 16 product takes ~16 tensor cycles, so the tensor pipe is ~10 % busy;
-// what bounds the kernel is the round trip of a ring stage (coefficient gather from L2, then the
-// products' completion) against the <= 160 KB that shared memory leaves for the ring. On the
-// 10,000-template, 2^19-sample workload (3.5 M candidates) it takes 1.13 ms, the per-candidate
-// mma.sync kernel, which loads the rows straight into registers, 1.00 ms: that one stays the default.
+// What bounds the kernel is the round trip of a ring stage (coefficient gather from L2, then the
+// products' completion) against the shared memory left for the ring (three 32-KB stages beside the
+// two 56-KB windows at k <= 256).
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -53,7 +56,8 @@ struct S2Params {
   const __half* alo;
   const float2* beta;  // [k][half] valid half
   int k, k16, kp2, nkb;  // kp2 = 2 k16 rounded up to kKB, nkb = kp2 / kKB
-  int stages;            // coefficient ring depth S
+  int stages;            // coefficient ring depth
+  int nbuf;              // window buffers (2: a piece's window is built while the one before runs)
   int T;
   int64_t half;
   int bin0;
@@ -99,7 +103,8 @@ __device__ __forceinline__ int tiles_of(const int4& pc) { return (int)(((unsigne
 
 template <int W, int N>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
-  static_assert(2 * W <= N, "columns");
+  constexpr int S = N / 2, G = S / W;  // samples and bins of a group
+  static_assert(G * W == S && G >= 1 && G <= 32 && N % 32 == 0 && 16 % W == 0, "a group is a whole number of bins");
   constexpr int N2 = 2 * N;  // B rows: hi window in 0..N-1, lo window in N..2N-1
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t afull[kMaxStagesA], aempty[kMaxStagesA], bfull[2], bempty[2], tfull[2], tempty[2],
@@ -113,13 +118,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
   static_assert(kCols <= 512 && (kCols & (kCols - 1)) == 0, "tensor-memory columns");
   const uint32_t base = (saddr(dsm) + 1023u) & ~1023u;
   constexpr uint32_t A_PLANE = kBM * 128, A_STAGE = kAStageBytes;
-  const int S = p.stages;
+  const int NS = p.stages;
   const uint32_t b_tile = N2 * 128, b_buf = (uint32_t)p.nkb * b_tile;
-  const uint32_t a0 = base, b0 = base + S * A_STAGE;
+  const uint32_t a0 = base, b0 = base + NS * A_STAGE;
   uint8_t* const gen = dsm + (base - saddr(dsm));  // generic pointer to `base`
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&afull[s], 128);
       mbar_init(&aempty[s], 1);
     }
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
       const int64_t lo_off = (int64_t)p.T * p2;
       bool ok = true;
       for (int kb = 0; kb < p.nkb; ++kb, ++g) {
-        const uint32_t s = g % S, ph = (g / S) & 1;
+        const uint32_t s = g % NS, ph = (g / NS) & 1;
         // every lane waits; the outcome is made warp-uniform before the warp-wide steps below
         if (!__all_sync(kFull, mbar_wait(&aempty[s], ph ^ 1, &abort_flag))) {
           if (lane == 0) fail();
@@ -224,8 +229,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
       for (unsigned pc_i = blockIdx.x; pc_i < npieces && !abort_flag; pc_i += grid, ++i) {
         const int4 pc = pcn;
         pcn = piece_at(p, pc_i + grid, npieces);
-        const int pb = i & 1;
-        if (!mbar_wait(&bfull[pb], (i >> 1) & 1, &abort_flag)) {
+        const int pb = i % p.nbuf;
+        if (!mbar_wait(&bfull[pb], (i / p.nbuf) & 1, &abort_flag)) {
           fail();
           break;
         }
@@ -243,7 +248,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)acc * kAcc;
           for (int kb = 0; kb < p.nkb; ++kb, ++g) {
-            const uint32_t s = g % S, ph = (g / S) & 1;
+            const uint32_t s = g % NS, ph = (g / NS) & 1;
             if (!mbar_wait(&afull[s], ph, &abort_flag)) {
               fail();
               ok = false;
@@ -285,10 +290,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
     for (unsigned pc_i = blockIdx.x; pc_i < npieces && !stop; pc_i += grid) {
       const int4 pc = pcn;
       pcn = piece_at(p, pc_i + grid, npieces);
-      const int bin = pc.x;
+      const int grp = pc.x;
       const unsigned c0 = (unsigned)pc.y, c1 = (unsigned)pc.z;
       const int ntiles = tiles_of(pc);
       for (int tile = 0; tile < ntiles; ++tile, ++gt) {
+        const unsigned ci = c0 + tile * kBM + q * 32 + lane;
+        rb::SortedCand cd{-1, 0, 0u};
+        if (ci < c1) cd = p.sorted[ci];
         const int acc = gt & 1;
         if (!__all_sync(kFull, mbar_wait(&tfull[acc], (gt >> 1) & 1, &abort_flag))) {
           if (lane == 0) fail();
@@ -296,43 +304,54 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
           break;
         }
         tc_fence_after();
-        float v[32];
-        tc_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * kAcc, v);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[acc]);
-        const unsigned ci = c0 + tile * kBM + q * 32 + lane;
-        float best = -1.f, zr = 0.f, zi = 0.f;
-        int br = 0;
+        // columns 0..N-1: products against the hi window, N..2N-1: against the lo window; read 32
+        // columns (16 samples, 16 / W bins) of each at a time
+        const uint32_t row = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * kAcc;
 #pragma unroll
-        for (int r = 0; r < W; ++r) {
-          const float re = v[2 * r] + v[N + 2 * r], im = v[2 * r + 1] + v[N + 2 * r + 1];
-          const float p2s = fmaf(re, re, im * im);
-          if (p2s > best) {
-            best = p2s;
-            br = r;
-            zr = re;
-            zi = im;
+        for (int h = 0; h < N / 32; ++h) {
+          float vh[32], vl[32];
+          tc_ld32(row + 32 * h, vh);
+          tc_ld32(row + N + 32 * h, vl);
+          if (h == N / 32 - 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
           }
-        }
-        const bool emit = ci < c1 && best >= p.thr2;
-        const unsigned em = __ballot_sync(kFull, emit);
-        if (!em) continue;
-        const int leader = __ffs(em) - 1;
-        unsigned long long b0c = 0;
-        if (lane == leader) b0c = atomicAdd(p.counter, (unsigned long long)__popc(em));
-        b0c = __shfl_sync(kFull, b0c, leader);
-        if (emit) {
-          const rb::SortedCand cd = p.sorted[ci];
-          const unsigned long long idx = b0c + __popc(em & ((1u << lane) - 1u));
-          if ((int64_t)idx < p.cap) {
-            rb_trigger tg;
-            tg.sample = p.sample_offset + (int64_t)(p.bin0 + bin) * W + br;
-            tg.tmpl = p.tmpl_base + cd.tmpl;
-            tg.block = cd.block;
-            tg.snr = sqrtf(best);
-            tg.phase = atan2f(zi, zr);
-            p.trig[idx] = tg;
+#pragma unroll
+          for (int j = h * (16 / W); j < (h + 1) * (16 / W); ++j) {
+            float best = -1.f, zr = 0.f, zi = 0.f;
+            int br = 0;
+#pragma unroll
+            for (int r = j * W; r < (j + 1) * W; ++r) {
+              const int c = 2 * (r - 16 * h);
+              const float re = vh[c] + vl[c], im = vh[c + 1] + vl[c + 1];
+              const float p2s = fmaf(re, re, im * im);
+              if (p2s > best) {
+                best = p2s;
+                br = r - j * W;
+                zr = re;
+                zi = im;
+              }
+            }
+            const bool emit = ci < c1 && ((cd.mask >> j) & 1u) && best >= p.thr2;
+            const unsigned em = __ballot_sync(kFull, emit);
+            if (!em) continue;
+            const int leader = __ffs(em) - 1;
+            unsigned long long b0c = 0;
+            if (lane == leader) b0c = atomicAdd(p.counter, (unsigned long long)__popc(em));
+            b0c = __shfl_sync(kFull, b0c, leader);
+            if (emit) {
+              const unsigned long long idx = b0c + __popc(em & ((1u << lane) - 1u));
+              if ((int64_t)idx < p.cap) {
+                rb_trigger tg;
+                tg.sample = p.sample_offset + (int64_t)(p.bin0 + grp * G + j) * W + br;
+                tg.tmpl = p.tmpl_base + cd.tmpl;
+                tg.block = cd.block;
+                tg.snr = sqrtf(best);
+                tg.phase = atan2f(zi, zr);
+                p.trig[idx] = tg;
+              }
+            }
           }
         }
       }
@@ -340,33 +359,34 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
   } else {
     // ---------------- window producers: B operand of each piece's bin, double-buffered
     const int tid = threadIdx.x - 9 * 32;  // 0..127
-    // zero both B buffers once: columns n >= 2W and positions >= 2 k16 are never written again
-    for (uint32_t o = tid * 16; o < 2 * b_buf; o += 128 * 16)
+    // zero both B buffers once: positions >= 2 k16 are never written again
+    for (uint32_t o = tid * 16; o < p.nbuf * b_buf; o += 128 * 16)
       *reinterpret_cast<uint4*>(gen + (b0 - base) + o) = make_uint4(0u, 0u, 0u, 0u);
     asm volatile("bar.sync 1, 128;" ::: "memory");
-    const int total = p.k16 * W;
+    const int total = p.k16 * S;
     int4 pcn = piece_at(p, blockIdx.x, npieces);
     unsigned i = 0;
     for (unsigned pc_i = blockIdx.x; pc_i < npieces && !abort_flag; pc_i += grid, ++i) {
-      const int bin = pcn.x;
+      const int grp = pcn.x;
       pcn = piece_at(p, pc_i + grid, npieces);
-      const int pb = i & 1;
-      if (!mbar_wait(&bempty[pb], ((i >> 1) & 1) ^ 1, &abort_flag)) {
+      const int pb = i % p.nbuf;
+      if (!mbar_wait(&bempty[pb], ((i / p.nbuf) & 1) ^ 1, &abort_flag)) {
         fail();
         break;
       }
-      const int64_t m0 = (int64_t)(p.bin0 + bin) * W - p.half;
+      const int64_t m0 = (int64_t)grp * S;  // valid-half index of the group's first sample
       uint8_t* bt = gen + (b0 - base) + pb * b_buf;
       for (int i0 = tid; i0 < total; i0 += 4 * 128) {
         float2 bv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {  // loads first, then the stores
-          const int idx = i0 + u * 128, kk = idx / W, r = idx - kk * W;
-          bv[u] = idx < total && kk < p.k ? __ldg(p.beta + (int64_t)kk * p.half + m0 + r) : make_float2(0.f, 0.f);
+        for (int u = 0; u < 4; ++u) {  // loads first, then the stores (zero past the valid half)
+          const int idx = i0 + u * 128, kk = idx / S, r = idx - kk * S;
+          bv[u] = idx < total && kk < p.k && m0 + r < p.half ? __ldg(p.beta + (int64_t)kk * p.half + m0 + r)
+                                                             : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int idx = i0 + u * 128, kk = idx / W, r = idx - kk * W;
+          const int idx = i0 + u * 128, kk = idx / S, r = idx - kk * S;
           if (idx >= total) break;
           // (column, n, value): Re half at column kk, Im half at column k16 + kk
           const float vals[4] = {bv[u].x, bv[u].y, bv[u].y, -bv[u].x};
@@ -395,6 +415,19 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
   }
 }
 
+// Shared memory of nbuf B windows of N = 2S columns, and the coefficient ring stages that fit beside
+// them.
+int window_bytes(int k, int N, int nbuf) {
+  const int k16 = (k + 15) / 16 * 16, nkb = (2 * k16 + kKB - 1) / kKB;
+  return nbuf * nkb * 2 * N * 128;
+}
+int ring_stages(int k, int N, int nbuf) {
+  const int limit = 227 * 1024 - 1024 - 256;  // 256: static barriers
+  return std::max(0, std::min(kMaxStagesA, (limit - window_bytes(k, N, nbuf)) / kAStageBytes));
+}
+// Window buffers for S samples: two while a ring of three stages still fits beside them, else one.
+int window_buffers(int k, int S) { return ring_stages(k, 2 * S, 2) >= 3 ? 2 : 1; }
+
 template <int W, int N>
 int launch_tc2(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
                const float2* beta, rb_trigger* trig, int64_t cap, unsigned long long* counter, cudaStream_t st,
@@ -422,13 +455,13 @@ int launch_tc2(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g
   p.flags = ws.flags;
   p.withhold_copies = withhold;
   p.idesc = (1u << 4) | ((uint32_t)((2 * N) >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);  // F32 acc, FP16 A/B
-  const int b_bytes = 2 * p.nkb * 2 * N * 128, limit = 227 * 1024 - 1024 - 256;  // 256: static barriers
-  p.stages = std::min(kMaxStagesA, (limit - b_bytes) / kAStageBytes);
+  p.nbuf = window_buffers(d.k, N / 2);
+  p.stages = ring_stages(d.k, N, p.nbuf);
   if (p.stages < 2) {
     rb::set_detail("k = %d too large for the tensor-core second stage", d.k);
     return RB_ERR_UNSUPPORTED;
   }
-  const int smem = p.stages * kAStageBytes + b_bytes + 1024;
+  const int smem = p.stages * kAStageBytes + window_bytes(d.k, N, p.nbuf) + 1024;
   auto kern = k_stage2_tc<W, N>;
   RB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   kern<<<152, kThreadsTc, smem, st>>>(p);
@@ -449,14 +482,25 @@ int stage2_tc_run(const rb_filter_desc& d, const rb_basis& b, const Geometry& g,
   while (left > 0 && !g_withhold2.compare_exchange_weak(left, left - 1)) {
   }
   const int withhold = left > 0 ? 1 : 0;
-  switch (d.w) {
-    case 1: return launch_tc2<1, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold, tmpl_base);
-    case 2: return launch_tc2<2, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold, tmpl_base);
-    case 4: return launch_tc2<4, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold, tmpl_base);
-    case 8: return launch_tc2<8, 16>(d, b, g, ws, beta, trig, cap, counter, st, withhold, tmpl_base);
-  }
-  set_detail("the tensor-core second stage takes w <= 8");
+  const int S = stage2_tc_samples(d);
+#define RB_TC2(W_, S_) \
+  if (d.w == W_ && S == S_) return launch_tc2<W_, 2 * S_>(d, b, g, ws, beta, trig, cap, counter, st, withhold, tmpl_base);
+  RB_TC2(1, 16) RB_TC2(2, 16) RB_TC2(4, 16) RB_TC2(8, 16)
+  RB_TC2(2, 32) RB_TC2(4, 32) RB_TC2(8, 32)
+#undef RB_TC2
+  set_detail("the tensor-core second stage takes w <= 8 and k with room for its coefficient ring");
   return RB_ERR_UNSUPPORTED;
+}
+
+int stage2_tc_samples(const rb_filter_desc& d) {
+  if (d.w > 8) return 0;
+  const int mode = stage2_tc_mode();
+  auto fits = [&](int S) { return ring_stages(d.k, 2 * S, window_buffers(d.k, S)) >= 2; };
+  if (mode == 16 || mode == 32) return fits(mode) && mode / d.w <= 16 ? mode : 0;
+  // automatic: 16 samples. 32-sample groups gather fewer rows (1.1 M against 1.9 M records on the
+  // 10,000-template workload at w = 8) but leave room for one window buffer only, and the window
+  // builds between pieces then cost more than the gathers save (0.70 ms against 0.62 ms there).
+  return fits(16) ? 16 : 0;
 }
 
 }  // namespace rb

@@ -285,6 +285,54 @@ def test_stage2_order_independent_and_hot_bins(api):
     assert stats["both"] > 500
 
 
+@pytest.mark.parametrize("w", [1, 8, 16])
+def test_stage2_coefficient_ring_depths(api, w):
+    """The second stage's coefficient fragments reach the products either straight into registers or
+    through each lane's cp.async ring in shared memory (2 to 4 slots): the triggers are bit-identical
+    for every depth, on a hot bin (several pieces) and scattered candidates, and agree with the oracle."""
+    from paper_2110_13115_gb300 import _native as N
+
+    lib = N.load()
+    n, k, T = 1 << 14, 72, 1500
+    half, nb = n // 2, n // (2 * w)
+    a = _rand_coeff(T, k, 61).astype(np.complex64)
+    beta = inputs.complex_normal((k, half), 62).astype(np.complex64)
+    rng = np.random.default_rng(63)
+    hot = np.zeros(T, dtype=api.CANDIDATE_NP)
+    hot["tmpl"] = np.arange(T)
+    hot["bin"] = nb + 11
+    rest = np.zeros(900, dtype=api.CANDIDATE_NP)
+    rest["tmpl"] = rng.integers(0, T, 900)
+    rest["bin"] = nb + rng.integers(0, nb, 900)
+    cands = np.unique(np.concatenate([hot, rest]))
+    d = api.make_desc(1024.0, n, k, T, w=w, rho_ii=1.5, cand_capacity=1 << 14)
+    basis = api.Basis(_dev(np.zeros((k, half), np.complex64)), _dev(a), n)
+    api.rb_pack_coeff(d, basis)
+    depths = (0, 2, 3, 4) if w == 8 else (0, 3)
+    outs = []
+    try:
+        for depth in depths:
+            assert lib.rbx_set_stage2_ring(depth) == 0
+            buf, nt = api.rb_stage2(d, basis, _dev(beta), _dev(cands.view(np.uint8)), len(cands), capacity=1 << 15)
+            outs.append(api.triggers_numpy(buf, nt))
+    finally:
+        lib.rbx_set_stage2_ring(3)
+    assert lib.rbx_set_stage2_ring(5) == N.RB_ERR_BAD_INPUT
+    for o in outs[1:]:
+        assert len(o) == len(outs[0])
+        for f in ("tmpl", "sample", "snr", "phase", "block"):
+            assert np.array_equal(o[f], outs[0][f]), f
+    full = np.zeros((k, n), np.complex128)
+    full[:, half:] = beta
+    oc = np.zeros(len(cands), dtype=rb.CAND_DTYPE)
+    oc["template"] = cands["tmpl"]
+    oc["bin"] = cands["bin"]
+    ref = rb.stage2(a.astype(np.complex128), full, oc, w, 1.5)
+    zr = np.abs(np.conj(a.astype(np.complex128)) @ beta.astype(np.complex128))
+    stats = compare_triggers(outs[0], ref, w, 1.5, ref_rho=zr)
+    assert stats["both"] > 500, stats
+
+
 def test_bucketing_window_and_fallback(api):
     """Bucketing histograms each chunk of consecutive candidates over a 4096-bin window from the
     chunk's smallest bin; bins beyond it take the per-candidate path. With 8192 valid bins, candidates
@@ -324,13 +372,91 @@ def test_bucketing_window_and_fallback(api):
     assert stats["both"] > 1000
 
 
+def _runs(T, nb, rng, max_len=40):
+    """Candidates as the first stage writes them for clustered triggers: per template, runs of
+    consecutive (or every-other) bins in increasing order, starting anywhere, so runs cross the
+    second stage's bin groups at every offset."""
+    tm, bn = [], []
+    for t in range(T):
+        for _ in range(int(rng.integers(1, 4))):
+            step = int(rng.integers(1, 3))
+            length = int(rng.integers(1, max_len))
+            start = int(rng.integers(0, nb - step * length))
+            tm.append(np.full(length, t))
+            bn.append(nb + start + step * np.arange(length))
+    return np.concatenate(tm), np.concatenate(bn)
+
+
+@pytest.mark.parametrize("mode", [16, 32])
+@pytest.mark.parametrize("w", [1, 2, 4, 8])
+def test_stage2_tc_bin_groups(api, w, mode):
+    """The tcgen05 second stage buckets by groups of mode / w bins (16 at most; w = 1 with 32-sample
+    groups takes the mma.sync kernel): a run of one template over increasing bins of a group becomes
+    one record with a bin mask, whose coefficient row is gathered once. The
+    triggers are bit-identical whatever the candidate order (runs intact, shuffled, a run reversed, a
+    candidate repeated next to itself, which only repeats its triggers), agree with the oracle, and
+    with the per-bin mma.sync second stage within its rounding."""
+    from paper_2110_13115_gb300 import _native as N
+
+    lib = N.load()
+    n, k, T = 1 << 14, 40, 300
+    half, nb = n // 2, n // (2 * w)
+    a = _rand_coeff(T, k, 51).astype(np.complex64)
+    beta = inputs.complex_normal((k, half), 52).astype(np.complex64)
+    rng = np.random.default_rng(53)
+    tm, bn = _runs(T, nb, rng, max_len=min(40, nb // 4))
+    cands = np.zeros(len(tm), dtype=api.CANDIDATE_NP)
+    cands["tmpl"], cands["bin"] = tm, bn
+    _, first = np.unique(np.stack([tm, bn], 1), axis=0, return_index=True)
+    cands = cands[np.sort(first)]  # one candidate per (template, bin), runs in emission order
+    odd = np.concatenate([cands[:9][::-1], cands[9:20], cands[20:21], cands[20:]])
+    d = api.make_desc(1024.0, n, k, T, w=w, rho_ii=1.5, cand_capacity=1 << 16)
+    basis = api.Basis(_dev(np.zeros((k, half), np.complex64)), _dev(a), n)
+    api.rb_pack_coeff(d, basis)
+
+    def run(c, tc):
+        assert lib.rbx_set_stage2_tc(mode if tc else 0) == 0
+        c = np.ascontiguousarray(c)
+        buf, nt = api.rb_stage2(d, basis, _dev(beta), _dev(c.view(np.uint8)), len(c), capacity=1 << 16)
+        return api.triggers_numpy(buf, nt)
+
+    try:
+        got = run(cands, 1)
+        shuffled = run(cands[rng.permutation(len(cands))], 1)
+        odd_tc = run(odd, 1)
+        mma = run(cands, 0)
+    finally:
+        lib.rbx_set_stage2_tc(1)
+    assert len(shuffled) == len(got)
+    for f in ("tmpl", "sample", "snr", "phase", "block"):
+        assert np.array_equal(shuffled[f], got[f]), f
+    keys = lambda o: list(zip(o["tmpl"].tolist(), o["sample"].tolist(), o["snr"].tolist()))  # noqa: E731
+    rep = (int(cands[20]["tmpl"]), int(cands[20]["bin"]))
+    extra = sum(1 for t, smp, _ in keys(got) if (t, smp // w) == rep)
+    assert len(odd_tc) == len(got) + extra
+    assert set(keys(odd_tc)) == set(keys(got))
+    full = np.zeros((k, n), np.complex128)
+    full[:, half:] = beta
+    oc = np.zeros(len(cands), dtype=rb.CAND_DTYPE)
+    oc["template"] = cands["tmpl"]
+    oc["bin"] = cands["bin"]
+    ref = rb.stage2(a.astype(np.complex128), full, oc, w, 1.5)
+    zr = np.abs(np.conj(a.astype(np.complex128)) @ beta.astype(np.complex128))
+    stats = compare_triggers(got, ref, w, 1.5, ref_rho=zr)
+    assert stats["both"] > 1000, stats
+    ref2 = np.zeros(len(mma), dtype=mf.TRIGGER_DTYPE)
+    ref2["template"], ref2["sample"], ref2["snr"], ref2["phase"] = mma["tmpl"], mma["sample"], mma["snr"], mma["phase"]
+    compare_triggers(got, ref2, w, 1.5, ref_rho=zr)
+
+
 @pytest.mark.parametrize("w", [1, 2, 4, 8])
 @pytest.mark.parametrize("k", [24, 40, 256, 400])
 def test_stage2_tc_parity(api, w, k):
-    """The tcgen05 second stage (tiles of 128 candidates, hi and lo windows side by side in one
-    N = 32 operand, two products per K step) against the oracle and against the mma.sync second
-    stage on the same candidates, including a hot bin of several tiles. k = 400 leaves room for a
-    3-stage coefficient ring, k = 256 and below for 5."""
+    """The tcgen05 second stage (tiles of 128 records of a group of 16 / w bins, hi and lo windows side
+    by side in one N = 64 operand, two products per K step) against the oracle and against the
+    mma.sync second stage on the same candidates, including a hot bin of several tiles. k = 256 and
+    below leave room for a 3-stage coefficient ring; at k = 400 the windows leave too little, and the
+    call takes the mma.sync kernel."""
     from paper_2110_13115_gb300 import _native as N
 
     lib = N.load()
@@ -357,7 +483,7 @@ def test_stage2_tc_parity(api, w, k):
             buf, nt = api.rb_stage2(d, basis, _dev(beta), _dev(cands.view(np.uint8)), len(cands), capacity=1 << 14)
             outs.append(api.triggers_numpy(buf, nt))
     finally:
-        lib.rbx_set_stage2_tc(0)
+        lib.rbx_set_stage2_tc(1)
     got, mma = outs
     full = np.zeros((k, n), np.complex128)
     full[:, half:] = beta

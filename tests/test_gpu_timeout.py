@@ -104,4 +104,4 @@ def test_stage2_tc_bounded_wait_reports_timeout(api):
             assert np.array_equal(got[f], ref[f]), f
     finally:
         lib.rbx_stage2_withhold_copies(0)
-        lib.rbx_set_stage2_tc(0)
+        lib.rbx_set_stage2_tc(1)
