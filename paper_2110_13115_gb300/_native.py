@@ -146,6 +146,7 @@ HOST_HOOKS = {
     "rbx_stage2_withhold_copies": (C.c_int, [C.c_int]),
     "rbx_set_fft_radix32": (C.c_int, [C.c_int]),
     "rbx_set_stage2_ring": (C.c_int, [C.c_int]),
+    "rbx_set_stage2_tc_windows": (C.c_int, [C.c_int]),
 }
 
 _lib = None

@@ -75,15 +75,6 @@ struct S2Params {
   int tmpl_base;        // added to a trigger's template row (sub-banks filtered into one list)
 };
 
-// Packed column order of rb_pack_coeff: position p = 32 q + 8 t4 + s holds column
-// (2 q + s / 4) 16 + 2 t4 + (s & 1) + 8 ((s >> 1) & 1); this is its inverse.
-__device__ __forceinline__ int packed_pos(int col) {
-  const int kc = col >> 4, jj = col & 15;
-  const int q = kc >> 1, hb = kc & 1, t4 = (jj & 7) >> 1;
-  const int s = (jj & 1) + 2 * (jj >> 3) + 4 * hb;
-  return 32 * q + 8 * t4 + s;
-}
-
 // Byte offset of element e (0..63) of row `row` in a 128-byte swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw128_off(int row, int e) {
   return (uint32_t)(row * 128 + ((((e >> 3) ^ (row & 7))) << 4) + ((e & 7) << 1));
@@ -363,7 +354,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
     for (uint32_t o = tid * 16; o < p.nbuf * b_buf; o += 128 * 16)
       *reinterpret_cast<uint4*>(gen + (b0 - base) + o) = make_uint4(0u, 0u, 0u, 0u);
     asm volatile("bar.sync 1, 128;" ::: "memory");
-    const int total = p.k16 * S;
+    // one work item: the 16-byte chunk of packed positions 8 ch .. 8 ch + 7 (eight K columns) for
+    // sample r, both parts (B rows 2r and 2r + 1), hi and lo: eight beta loads, four 16-byte stores
+    const int nchunk = 2 * p.k16 / 8, total = nchunk * S;
     int4 pcn = piece_at(p, blockIdx.x, npieces);
     unsigned i = 0;
     for (unsigned pc_i = blockIdx.x; pc_i < npieces && !abort_flag; pc_i += grid, ++i) {
@@ -376,28 +369,57 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
       }
       const int64_t m0 = (int64_t)grp * S;  // valid-half index of the group's first sample
       uint8_t* bt = gen + (b0 - base) + pb * b_buf;
-      for (int i0 = tid; i0 < total; i0 += 4 * 128) {
-        float2 bv[4];
+      constexpr int U = 2;
+      for (int i0 = tid; i0 < total; i0 += U * 128) {
+        float2 bv[U][8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {  // loads first, then the stores (zero past the valid half)
-          const int idx = i0 + u * 128, kk = idx / S, r = idx - kk * S;
-          bv[u] = idx < total && kk < p.k && m0 + r < p.half ? __ldg(p.beta + (int64_t)kk * p.half + m0 + r)
-                                                             : make_float2(0.f, 0.f);
+        for (int u = 0; u < U; ++u) {  // loads first, then the stores (zero past the valid half)
+          const int idx = i0 + u * 128, ch = idx / S, r = idx - ch * S;
+          const bool in = idx < total && m0 + r < p.half;
+#pragma unroll
+          for (int sl = 0; sl < 8; ++sl) {
+            // packed position 8 ch + sl holds column (2 q + sl / 4) 16 + 2 t4 + (sl & 1) + 8 ((sl >> 1) & 1)
+            const int q = ch >> 2, t4 = ch & 3;
+            const int col = (2 * q + (sl >> 2)) * 16 + 2 * t4 + (sl & 1) + 8 * ((sl >> 1) & 1);
+            const int kk = col < p.k16 ? col : col - p.k16;
+            bv[u][sl] = in && kk < p.k ? __ldg(p.beta + (int64_t)kk * p.half + m0 + r) : make_float2(0.f, 0.f);
+          }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int idx = i0 + u * 128, kk = idx / S, r = idx - kk * S;
+        for (int u = 0; u < U; ++u) {
+          const int idx = i0 + u * 128, ch = idx / S, r = idx - ch * S;
           if (idx >= total) break;
-          // (column, n, value): Re half at column kk, Im half at column k16 + kk
-          const float vals[4] = {bv[u].x, bv[u].y, bv[u].y, -bv[u].x};
+          const int q = ch >> 2, t4 = ch & 3;
+          uint32_t h[2][4], l[2][4];  // [part][pair of halves]
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int col = (e < 2 ? 0 : p.k16) + kk, n = 2 * r + (e & 1);
-            const int pos = packed_pos(col);
-            uint8_t* kt = bt + (uint32_t)(pos / kKB) * b_tile;
-            const __half h = __float2half_rn(vals[e]);
-            *reinterpret_cast<__half*>(kt + sw128_off(n, pos % kKB)) = h;
-            *reinterpret_cast<__half*>(kt + sw128_off(N + n, pos % kKB)) = __float2half_rn(vals[e] - __half2float(h));
+          for (int sl = 0; sl < 8; sl += 2) {
+            __half hv[2][2], lv[2][2];
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+              const int e = sl + o;
+              const int col = (2 * q + (e >> 2)) * 16 + 2 * t4 + (e & 1) + 8 * ((e >> 1) & 1);
+              const float2 v = bv[u][e];
+              // Re half: (Re, Im) of beta; Im half: (Im, -Re)
+              const float x0 = col < p.k16 ? v.x : v.y, x1 = col < p.k16 ? v.y : -v.x;
+              hv[0][o] = __float2half_rn(x0);
+              lv[0][o] = __float2half_rn(x0 - __half2float(hv[0][o]));
+              hv[1][o] = __float2half_rn(x1);
+              lv[1][o] = __float2half_rn(x1 - __half2float(hv[1][o]));
+            }
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+              h[part][sl >> 1] = (uint32_t)__half_as_ushort(hv[part][0]) | ((uint32_t)__half_as_ushort(hv[part][1]) << 16);
+              l[part][sl >> 1] = (uint32_t)__half_as_ushort(lv[part][0]) | ((uint32_t)__half_as_ushort(lv[part][1]) << 16);
+            }
+          }
+          const int pos = 8 * ch;
+          uint8_t* kt = bt + (uint32_t)(pos / kKB) * b_tile;
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            const int n = 2 * r + part;
+            *reinterpret_cast<uint4*>(kt + sw128_off(n, pos % kKB)) = make_uint4(h[part][0], h[part][1], h[part][2], h[part][3]);
+            *reinterpret_cast<uint4*>(kt + sw128_off(N + n, pos % kKB)) =
+                make_uint4(l[part][0], l[part][1], l[part][2], l[part][3]);
           }
         }
       }
@@ -425,8 +447,14 @@ int ring_stages(int k, int N, int nbuf) {
   const int limit = 227 * 1024 - 1024 - 256;  // 256: static barriers
   return std::max(0, std::min(kMaxStagesA, (limit - window_bytes(k, N, nbuf)) / kAStageBytes));
 }
+std::atomic<int> g_windows{0};  // forced window buffers (0: automatic)
+
 // Window buffers for S samples: two while a ring of three stages still fits beside them, else one.
-int window_buffers(int k, int S) { return ring_stages(k, 2 * S, 2) >= 3 ? 2 : 1; }
+int window_buffers(int k, int S) {
+  const int forced = g_windows.load();
+  if (forced) return forced;
+  return ring_stages(k, 2 * S, 2) >= 3 ? 2 : 1;
+}
 
 template <int W, int N>
 int launch_tc2(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry& g, const rb::Workspace& ws,
@@ -510,5 +538,14 @@ int stage2_tc_samples(const rb_filter_desc& d) {
 // the context stays usable. Used by the failure-detection test; no other code calls it.
 extern "C" int rbx_stage2_withhold_copies(int n) {
   g_withhold2.store(n > 0 ? n : 0);
+  return 0;
+}
+
+// Host-only hook (not part of the C ABI): window buffers of the tcgen05 second stage, 1 or 2 (a
+// piece's window built while the one before runs), or 0 for the automatic choice; one buffer leaves
+// room for more coefficient-ring stages. RB_ERR_BAD_INPUT for another value.
+extern "C" int rbx_set_stage2_tc_windows(int n) {
+  if (n < 0 || n > 2) return RB_ERR_BAD_INPUT;
+  g_windows.store(n);
   return 0;
 }
