@@ -943,7 +943,7 @@ def main():
     descs, bases = descs_for(rho_i, wl.rho_ii)
     for d, sb in zip(descs, subs):
         api.rb_pack_coeff(d, sb["basis"])
-    ws = api.banks_workspace(descs)
+    ws = api.banks_workspace(descs, host=True)  # sized for the end-to-end call's host buffers too
     # autotune the FFT schedule (shared by every sub-bank of this n and w) and each sub-bank's
     # first-stage tile (setup, untimed)
     sh = api.rb_whiten(descs[0], strain_d, psd_d, ws=ws)

@@ -117,8 +117,9 @@ typedef struct rb_filter_sizes {
   int32_t n1, n2;           /* four-step split n = n1 * n2 */
   int32_t kp;               /* stage-1 contraction length 2k rounded up to 64 */
   size_t coeff_op_bytes;    /* bytes rb_pack_coeff writes for desc->precision */
-  int64_t host_trig_capacity; /* largest rb_filter capacity with RB_MEM_HOST_TRIGGERS (staging in the
-                                 workspace's four-step intermediate, free during the second stage) */
+  int64_t host_trig_capacity; /* largest rb_filter capacity with RB_MEM_HOST_TRIGGERS: the triggers are
+                                 staged in a region of max(96 MB, 8 n bytes) that the workspace holds
+                                 (workspace_bytes includes it) when desc->mem has that bit */
 } rb_filter_sizes;
 
 /* Name of a status code (static string). */
@@ -255,6 +256,9 @@ int rb_banks_plan(const rb_filter_desc* descs, int32_t n_banks, rb_filter_sizes*
  *     buffers as for rb_filter.
  *   bases: [n_banks] HOST array; bases[b] matches descs[b] and is packed by rb_pack_coeff for it.
  *   strain, psd, trig, capacity, n_trig: as rb_filter.   workspace: rb_banks_plan size.
+ *   With RB_MEM_HOST_TRIGGERS each sub-bank's triggers are copied out on a library-owned side stream
+ *   (one per device, kept for the life of the process) while the next sub-bank runs on `stream`; the
+ *   call returns when every copy has landed.
  *   Errors: as rb_filter; a sub-bank's candidate overflow sets *n_trig = -1 (RB_ERR_OVERFLOW).
  */
 int rb_filter_banks(const rb_filter_desc* descs, const rb_basis* bases, int32_t n_banks, const float* strain,

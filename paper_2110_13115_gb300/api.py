@@ -43,8 +43,17 @@ def rb_filter_plan(desc) -> N.rb_filter_sizes:
     return out
 
 
-def workspace(desc, device="cuda") -> torch.Tensor:
-    return torch.empty(rb_filter_plan(desc).workspace_bytes, dtype=torch.uint8, device=device)
+def _with_host_mem(desc):
+    d = N.rb_filter_desc.from_buffer_copy(desc)
+    d.mem = N.RB_MEM_HOST_STRAIN | N.RB_MEM_HOST_TRIGGERS
+    return d
+
+
+def workspace(desc, device="cuda", host=False) -> torch.Tensor:
+    """Workspace for desc; host=True sizes it for calls with host buffers (desc.mem set), which also
+    serves the device-buffer calls."""
+    d = _with_host_mem(desc) if host else desc
+    return torch.empty(rb_filter_plan(d).workspace_bytes, dtype=torch.uint8, device=device)
 
 
 @dataclasses.dataclass
@@ -163,11 +172,10 @@ def rb_filter_host(desc, basis: Basis, strain, psd: torch.Tensor, trig, capacity
     the library copies the strain in and the triggers out on the current stream inside the one call.
     strain: float32 [n] host buffer; trig: host buffer of `capacity` records (TRIGGER_NP numpy array
     or a uint8 CPU tensor of capacity * 24 bytes). Returns the trigger count."""
-    ws = workspace(desc) if ws is None else ws
+    ws = workspace(desc, host=True) if ws is None else ws
     if capacity is None:
         capacity = len(trig) if isinstance(trig, np.ndarray) and trig.dtype == TRIGGER_NP else trig.numel() // 24
-    d = N.rb_filter_desc.from_buffer_copy(desc)
-    d.mem = N.RB_MEM_HOST_STRAIN | N.RB_MEM_HOST_TRIGGERS
+    d = _with_host_mem(desc)
     n = C.c_int64(0)
     b = basis.c_struct()
     rc = _lib().rb_filter(C.byref(d), C.byref(b), _host_ptr(strain), _p(psd), _host_ptr(trig), int(capacity),
@@ -185,15 +193,17 @@ def rb_banks_plan(descs) -> N.rb_filter_sizes:
     return out
 
 
-def banks_workspace(descs, device="cuda") -> torch.Tensor:
-    return torch.empty(rb_banks_plan(descs).workspace_bytes, dtype=torch.uint8, device=device)
+def banks_workspace(descs, device="cuda", host=False) -> torch.Tensor:
+    """Workspace for rb_filter_banks; host=True sizes it for host buffers (it serves both kinds)."""
+    ds = [_with_host_mem(d) for d in descs] if host else descs
+    return torch.empty(rb_banks_plan(ds).workspace_bytes, dtype=torch.uint8, device=device)
 
 
 def rb_filter_banks(descs, bases, strain, psd: torch.Tensor, capacity=1 << 22, ws=None, trig=None, host=False):
     """One block through every sub-bank (whitened once); returns (trigger buffer, count). Template rows
     of the triggers index the concatenation of the sub-banks. With host=True, `strain` and `trig` are
     host buffers (numpy or CPU tensors) and the library copies them on the current stream."""
-    ws = banks_workspace(descs) if ws is None else ws
+    ws = banks_workspace(descs, host=host) if ws is None else ws
     descs = [N.rb_filter_desc.from_buffer_copy(d) for d in descs]
     for d in descs:
         d.mem = (N.RB_MEM_HOST_STRAIN | N.RB_MEM_HOST_TRIGGERS) if host else 0

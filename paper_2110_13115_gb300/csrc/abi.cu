@@ -10,6 +10,8 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <atomic>
 #include <memory>
 #include <vector>
@@ -126,6 +128,11 @@ size_t coeff_op_bytes(const rb_filter_desc& d, const Geometry& g) {
   return g.s2_bytes + stage1;
 }
 
+// Bytes of the trigger staging region for host trigger buffers: 96 MB, at least one n-point vector.
+size_t host_trig_bytes(const Geometry& g) {
+  return std::max<size_t>(size_t(96) << 20, sizeof(float2) * (size_t)g.n) / sizeof(rb_trigger) * sizeof(rb_trigger);
+}
+
 void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws, bool plain) {
   size_t off = 0;
   auto take = [&](size_t bytes) -> char* {
@@ -151,6 +158,8 @@ void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws
   ws->tables.w2b = ws->tables.w2b_w;
   ws->wt = (float*)take(sizeof(float) * half);
   ws->shat = (float2*)take(sizeof(float2) * half);
+  // everything above depends on n only, so sub-banks that share a workspace share it
+  if (!plain && (d.mem & RB_MEM_HOST_TRIGGERS)) ws->trig_stage = (rb_trigger*)take(host_trig_bytes(g));
   const int64_t nvec = plain ? d.n_templates : d.k;
   int64_t vc = (int64_t(96) << 20) / (g.n * 8);  // four-step chunks of up to 96 MB (kept in L2)
   vc = std::max<int64_t>(1, std::min<int64_t>(vc, std::min<int64_t>(nvec, 65535)));
@@ -182,10 +191,27 @@ using namespace rb;
 
 namespace {
 
-// Triggers rb_filter can stage on the device for a host trigger buffer: the four-step intermediate X
-// ([vc][n] complex) is idle from the end of the basis filter on.
-int64_t host_trig_capacity(const Geometry& g, const Workspace& ws) {
-  return (int64_t)(sizeof(float2) * (size_t)g.n * ws.vc / sizeof(rb_trigger));
+// Triggers rb_filter and rb_filter_banks can stage on the device for a host trigger buffer.
+int64_t host_trig_capacity(const Geometry& g, const Workspace&) {
+  return (int64_t)(host_trig_bytes(g) / sizeof(rb_trigger));
+}
+
+// A non-blocking stream per device for the trigger copies of rb_filter_banks, created on first use
+// and kept for the life of the process.
+int copy_stream(cudaStream_t* out) {
+  static std::mutex mu;
+  static std::map<int, cudaStream_t> streams;
+  int dev = 0;
+  RB_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = streams.find(dev);
+  if (it == streams.end()) {
+    cudaStream_t s = nullptr;
+    RB_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    it = streams.emplace(dev, s).first;
+  }
+  *out = it->second;
+  return RB_OK;
 }
 
 int prepare(const rb_filter_desc* desc, void* workspace, size_t bytes, bool plain, Geometry* g, Workspace* ws,
@@ -722,14 +748,14 @@ int rb_filter(const rb_filter_desc* desc, const rb_basis* basis, const float* st
     return RB_ERR_BAD_INPUT;
   }
   // host buffers: the strain is staged in the beta region (written only after the whitening FFT
-  // has read it) and the triggers in the four-step intermediate (free once the basis filter is done)
+  // has read it) and the triggers in the staging region
   const bool host_in = desc->mem & RB_MEM_HOST_STRAIN, host_out = desc->mem & RB_MEM_HOST_TRIGGERS;
   if (host_out && capacity > host_trig_capacity(g, ws)) {
     set_detail("capacity %lld exceeds host_trig_capacity %lld", (long long)capacity,
                (long long)host_trig_capacity(g, ws));
     return RB_ERR_BAD_INPUT;
   }
-  rb_trigger* trig_d = host_out ? reinterpret_cast<rb_trigger*>(ws.X) : trig;
+  rb_trigger* trig_d = host_out ? ws.trig_stage : trig;
   StageMarks mk;
   mk.begin(st);
   if (host_in) {
@@ -851,7 +877,37 @@ int rb_filter_banks(const rb_filter_desc* descs, const rb_basis* bases, int32_t 
   if ((rc = make_geometry(descs[0], &g0))) return rc;
   carve(descs[0], g0, (char*)workspace, &ws0, false);
   RB_CUDA_TRY(cudaMemsetAsync(ws0.flags, 0, 256, st));
-  rb_trigger* trig_d = host_out ? reinterpret_cast<rb_trigger*>(ws0.X) : trig;
+  rb_trigger* trig_d = host_out ? ws0.trig_stage : trig;
+  // host triggers: once sub-bank b is done (its event), its triggers go out on a side stream while the
+  // sub-banks after it run on `stream`; the staging region is not touched by later sub-banks except
+  // past their own count
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> done;
+  struct EventGuard {
+    std::vector<cudaEvent_t>& ev;
+    ~EventGuard() {
+      for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+  } guard{done};
+  if (host_out) {
+    if ((rc = copy_stream(&cs))) return rc;
+    done.resize(n_banks, nullptr);
+    for (auto& e : done) RB_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  int64_t copied = 0;
+  // copies sub-bank j's new triggers (blocks the host until sub-bank j is done)
+  auto flush = [&](int j) -> int {
+    unsigned long long cnt = 0;
+    RB_CUDA_TRY(cudaStreamWaitEvent(cs, done[j], 0));
+    RB_CUDA_TRY(cudaMemcpyAsync(&cnt, ws0.trig_count, sizeof(cnt), cudaMemcpyDeviceToHost, cs));
+    RB_CUDA_TRY(cudaStreamSynchronize(cs));
+    const int64_t upto = std::min<int64_t>((int64_t)cnt, capacity);
+    if (upto > copied)
+      RB_CUDA_TRY(cudaMemcpyAsync(trig + copied, trig_d + copied, sizeof(rb_trigger) * (upto - copied),
+                                  cudaMemcpyDeviceToHost, cs));
+    copied = std::max(copied, upto);
+    return RB_OK;
+  };
   StageMarks mk;
   mk.begin(st);
   if (host_in) {
@@ -861,7 +917,7 @@ int rb_filter_banks(const rb_filter_desc* descs, const rb_basis* bases, int32_t 
   if ((rc = init_tables(g0, ws0, psd, descs[0].fs, st))) return rc;
   mk.to(RB_STAGE_WHITEN);
   if ((rc = whiten(g0, ws0, strain, ws0.shat, st))) return rc;
-  int64_t copied = 0, base = 0;
+  int64_t base = 0;
   Status s{};
   for (int32_t b = 0; b < n_banks; ++b) {
     rb_filter_desc d = descs[b];
@@ -886,15 +942,13 @@ int rb_filter_banks(const rb_filter_desc* descs, const rb_basis* bases, int32_t 
     mk.finish();
     base += d.n_templates;
     if (host_out) {
-      // the staging area is the next sub-bank's four-step intermediate: copy this sub-bank's triggers
-      // out (stream-ordered before that sub-bank's basis filter) once their count is known
-      if ((rc = read_status(ws0, &s, st))) return rc;
-      const int64_t upto = std::min<int64_t>((int64_t)s.trig, capacity);
-      if (upto > copied)
-        RB_CUDA_TRY(cudaMemcpyAsync(trig + copied, trig_d + copied, sizeof(rb_trigger) * (upto - copied),
-                                    cudaMemcpyDeviceToHost, st));
-      copied = std::max(copied, upto);
+      RB_CUDA_TRY(cudaEventRecord(done[b], st));
+      if (b > 0 && (rc = flush(b - 1))) return rc;  // sub-bank b is queued behind it meanwhile
     }
+  }
+  if (host_out) {
+    if ((rc = flush(n_banks - 1))) return rc;
+    RB_CUDA_TRY(cudaStreamSynchronize(cs));
   }
   if ((rc = read_status(ws0, &s, st))) return rc;
   if (s.flags & RB_FLAG_BAD_PSD) {

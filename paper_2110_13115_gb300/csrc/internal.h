@@ -56,6 +56,8 @@ struct Workspace {
   Tables tables;
   float* wt = nullptr;        // [n/2] whitening weights
   float2* shat = nullptr;     // [n/2] whitened data
+  rb_trigger* trig_stage = nullptr;  // device staging of the triggers for RB_MEM_HOST_TRIGGERS (at an
+                                     // offset and size that depend on n only)
   float2* X = nullptr;        // [vc][n1][n2] four-step intermediate
   int vc = 1;                 // vectors per four-step chunk
   float2* beta = nullptr;     // [k][n/2]

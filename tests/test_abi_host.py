@@ -99,9 +99,10 @@ def test_plan_validation(lib):
     assert rc == 0 and s3.coeff_op_bytes == 2 * 10000 * 512 * 2
     # beta (k n/2 complex64) dominates the workspace
     assert s2.workspace_bytes >= 256 * 262144 * 8
-    # host trigger staging: the four-step intermediate, chunks of up to 96 MB of n-sample vectors
-    vc = min((96 << 20) // (524288 * 8), 256)
-    assert s2.host_trig_capacity == vc * 524288 * 8 // 24
+    # host trigger staging: a region of max(96 MB, 8 n bytes), carved only when mem asks for host triggers
+    assert s2.host_trig_capacity == (96 << 20) // 24
+    rc, s4 = plan(n=524288, k=256, n_templates=10000, precision="fp16_split", mem=N.RB_MEM_HOST_TRIGGERS)
+    assert rc == 0 and s4.workspace_bytes == s2.workspace_bytes + (96 << 20) // 24 * 24
     assert plan(mem=N.RB_MEM_HOST_STRAIN | N.RB_MEM_HOST_TRIGGERS)[0] == 0
     assert plan(mem=4)[0] == N.RB_ERR_BAD_INPUT
     assert lib.rb_strerror(N.RB_ERR_OVERFLOW) == b"output overflow"

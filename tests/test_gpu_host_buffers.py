@@ -46,7 +46,7 @@ def test_host_buffers_match_device_call_numpy(api, case):
     strain = np.ascontiguousarray(wl.strain, dtype=np.float32)
     cap = 1 << 14
     trig = np.zeros(cap, dtype=api.TRIGGER_NP)
-    ws = api.workspace(d)
+    ws = api.workspace(d, host=True)
     dh = N.rb_filter_desc.from_buffer_copy(d)
     dh.mem = N.RB_MEM_HOST_STRAIN | N.RB_MEM_HOST_TRIGGERS
     n = C.c_int64(0)
@@ -72,7 +72,7 @@ def test_host_buffers_pinned_and_one_sided(api, case):
     n = api.rb_filter_host(d, basis, strain_h, psd, trig_h)
     got = np.sort(trig_h[: n * 24].numpy().view(api.TRIGGER_NP), order=["tmpl", "sample"])
     assert np.array_equal(got, ref)
-    ws = api.workspace(d)
+    ws = api.workspace(d, host=True)
     for mem in (N.RB_MEM_HOST_STRAIN, N.RB_MEM_HOST_TRIGGERS):
         dh = N.rb_filter_desc.from_buffer_copy(d)
         dh.mem = mem
