@@ -147,6 +147,7 @@ HOST_HOOKS = {
     "rbx_set_fft_radix32": (C.c_int, [C.c_int]),
     "rbx_set_stage2_ring": (C.c_int, [C.c_int]),
     "rbx_set_stage2_tc_windows": (C.c_int, [C.c_int]),
+    "rbx_mma_sync_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
 }
 
 _lib = None

@@ -653,3 +653,47 @@ extern "C" int rbx_set_stage2_tc(int mode) {
   g_stage2_tc.store(mode);
   return 0;
 }
+
+// Host-only measurement hook (not part of the C ABI): the mma.sync m16n8k16 FP16 -> FP32 issue rate of
+// this GPU, the ceiling of the mma.sync second stage. Every warp of 608 CTAs x 256 threads runs `iters`
+// rounds of 8 independent register-only products; *per_s receives products per second (0 on error).
+namespace {
+__global__ void __launch_bounds__(256) k_mma_rate(float* out, int iters) {
+  uint32_t a0 = threadIdx.x * 2654435761u, a1 = a0 * 3u, a2 = a0 * 5u, a3 = a0 * 7u, b0 = a0 * 11u, b1 = a0 * 13u;
+  float d[8][4] = {};
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mma16816(d[i], a0, a1, a2, a3, b0, b1);
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc += d[i][0] + d[i][1] + d[i][2] + d[i][3];
+  if (acc == 1.2345f) out[0] = acc;  // keeps the products live
+}
+}  // namespace
+
+extern "C" int rbx_mma_sync_rate(int iters, double* per_s) {
+  if (!per_s || iters < 1 || iters > (1 << 20)) return RB_ERR_BAD_INPUT;
+  *per_s = 0.0;
+  float* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = RB_OK;
+  float ms = 0.f;
+  if (cudaMalloc(&out, sizeof(float)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    rc = RB_ERR_CUDA;
+  } else {
+    k_mma_rate<<<608, 256>>>(out, iters);  // warm-up
+    cudaEventRecord(e0);
+    k_mma_rate<<<608, 256>>>(out, iters);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f)
+      rc = RB_ERR_CUDA;
+    else
+      *per_s = 608.0 * 8 * iters * 8 / (ms * 1e-3);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (out) cudaFree(out);
+  return rc;
+}

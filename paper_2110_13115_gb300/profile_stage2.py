@@ -1,6 +1,6 @@
 """Timing driver of the second stage on real clustered candidates, for profiling it alone.
 
-``python -m paper_2110_13115_gb300.profile_stage2 [samples ...]`` takes the full-size block (10,000
+``python -m paper_2110_13115_gb300.profile_stage2 [kernel ...]`` takes the full-size block (10,000
 templates, 256 s at 2048 Hz, w = 8, 20 injections), the first of its four tau0 sub-banks (2,500
 templates) with a GPU basis of at most 320 vectors truncated to the fewest that hold every template's
 SNR loss within 1e-3, and its first-stage candidates at rho_I = 4.378 (FP16 split-A); then, for each
@@ -8,10 +8,12 @@ second-stage kernel given ("tc": the tcgen05 kernel over bin groups of the autom
 or "tc32": of 16 or 32 samples; a number: the mma.sync kernel with that coefficient-ring depth, 0
 for loads into registers, else 2, 3 or 4 slots; "tc 2" if none), two warm-up rb_stage2 calls and
 five timed ones. Prints the candidates and the milliseconds per call (bucketing + reconstruction)
-for each.
+for each, then the GPU's mma.sync m16n8k16 FP16 issue rate (register-only products, the ceiling of
+the mma.sync kernel).
 """
 from __future__ import annotations
 
+import ctypes
 import sys
 
 import numpy as np
@@ -65,6 +67,10 @@ def main(argv):
     finally:
         lib.rbx_set_stage2_tc(1)
         lib.rbx_set_stage2_ring(2)
+    rate = ctypes.c_double(0.0)
+    _native.check("rbx_mma_sync_rate", lib.rbx_mma_sync_rate(4000, ctypes.byref(rate)))
+    print(f"mma.sync m16n8k16 FP16: {rate.value / 1e9:.1f} G products/s = {rate.value * 4096 * 2 / 1e12:.0f} TFLOP/s",
+          flush=True)
 
 
 if __name__ == "__main__":
