@@ -114,18 +114,20 @@ __global__ void __launch_bounds__(256) k_bin_count(const rb_candidate* __restric
   }
 }
 
-constexpr int kScanPer = 4;                  // counters per thread and tile
-constexpr int kScanTile = 1024 * kScanPer;   // bins per tile
-__host__ __device__ constexpr int spad(int x) { return x + (x >> 5); }  // conflict-free per-thread runs
+constexpr int kScanPer = 16;                 // counters per thread and tile
+constexpr int kScanTile = 1024 * kScanPer;   // bins per tile (one tile for 2^19-sample blocks at w = 8)
+// one padding word per kScanPer: each thread's run of kScanPer counters starts in its own bank
+__host__ __device__ constexpr int spad(int x) { return x + x / kScanPer; }
+constexpr size_t kScanSmem = 2 * sizeof(unsigned) * (spad(kScanTile) + 1);
 
 // Exclusive scan of count[0, nb) into start[0, nb] plus the piece list; count is reset to zero
 // (it becomes the per-bin fill cursor). A bin holding c candidates is cut into ceil(c / kPiece)
 // pieces {bin, first, end} of at most kPiece consecutive bucketed candidates, so that the
 // second stage can spread a bin with thousands of candidates over many CTAs and skips empty
 // bins entirely. Counts and piece counts are scanned together as one 64-bit value (pieces in the
-// high word). One CTA of 1024 threads walks the array in tiles of 4096 counters, loading the next
+// high word). One CTA of 1024 threads walks the array in tiles of 16384 counters, loading the next
 // tile's counters while it processes one. Counters and start[] move with coalesced accesses
-// through shared memory; each thread scans 4 consecutive counters; the tile's pieces are written
+// through shared memory; each thread scans 16 consecutive counters; the tile's pieces are written
 // one per thread (coalesced), each thread finding its piece's bin by binary search over the tile's
 // piece prefix. Also raises
 // RB_FLAG_CAND_OVERFLOW when the first stage found more candidates than the buffer holds.
@@ -134,8 +136,9 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
                                                    const unsigned long long* dev_count, int64_t cap,
                                                    unsigned* flags) {
   using u64 = unsigned long long;
-  __shared__ unsigned st_s[spad(kScanTile) + 1];  // global start of every bin of the tile (+ the end)
-  __shared__ unsigned pp_s[spad(kScanTile) + 1];  // global index of every bin's first piece (+ the end)
+  extern __shared__ unsigned scan_smem[];
+  unsigned* st_s = scan_smem;                          // global start of every bin of the tile (+ the end)
+  unsigned* pp_s = scan_smem + spad(kScanTile) + 1;   // global index of every bin's first piece (+ the end)
   __shared__ u64 wsum[32];
   __shared__ u64 carry_s, carry_next;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -163,13 +166,9 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
     for (int j = 0; j < kScanPer; ++j) st_s[spad(j * 1024 + tid)] = nx[j];
     fetch(base + kScanTile);
     __syncthreads();
-    unsigned v[kScanPer];
     u64 s = 0;
 #pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
-      v[j] = st_s[spad(tid * kScanPer + j)];
-      s += packed(v[j]);
-    }
+    for (int j = 0; j < kScanPer; ++j) s += packed(st_s[spad(tid * kScanPer + j)]);
     u64 inc = s;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -191,11 +190,12 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
     __syncthreads();
     u64 run = carry_s + wsum[warp] + inc - s;
 #pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
+    for (int j = 0; j < kScanPer; ++j) {  // (this thread's own counters: read, then overwritten)
       const int x = tid * kScanPer + j;
+      const unsigned c = st_s[spad(x)];
       st_s[spad(x)] = (unsigned)run;
       pp_s[spad(x)] = (unsigned)(run >> 32);
-      run += packed(v[j]);
+      run += packed(c);
     }
     if (tid == 1023) {  // bins past nb count 0, so this is the tile's end
       st_s[spad(kScanTile)] = (unsigned)run;
@@ -585,8 +585,9 @@ int stage2_bucket(const rb_filter_desc& d, const Geometry& g, const Workspace& w
   k_bin_count<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, gs,
                                        ws.bin_count);
   RB_LAUNCH_CHECK();
-  k_bin_scan<<<1, 1024, 0, st>>>(ws.bin_count, ws.bin_start, ng, ws.pieces, ws.piece_total, ws.cand_count,
-                                 d.cand_capacity, ws.flags);
+  RB_CUDA_TRY(cudaFuncSetAttribute(k_bin_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem));
+  k_bin_scan<<<1, 1024, kScanSmem, st>>>(ws.bin_count, ws.bin_start, ng, ws.pieces, ws.piece_total, ws.cand_count,
+                                         d.cand_capacity, ws.flags);
   RB_LAUNCH_CHECK();
   k_bin_scatter<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, gs,
                                          ws.bin_start, ws.bin_count, ws.cand_sorted);
