@@ -465,19 +465,23 @@ def cufft_basis_filter(torch, vectors, s_hat, n, w, chunk=16, reps=3):
                 chunk=chunk)
 
 
-def refine_rate(api, torch, n_cand=1024, steps=20, reps=3):
-    """Candidate refinement (a8) on the tiny workload (16-s block at 1024 Hz): n_cand candidates around
-    its injection (the bank templates' chirp mass and eta, coalescence time within a few ms of the
-    injected one, random phase), `steps` gradient-ascent steps each; candidates refined per second."""
+def refine_rate(api, torch, n_cand=1024, steps=20, reps=3, wl=None):
+    """Candidate refinement (a8): n_cand candidates around the workload's injections (the bank
+    templates' chirp mass and eta, coalescence time within a few ms of an injected one, random phase),
+    `steps` gradient-ascent steps each; candidates refined per second. Default: the tiny workload
+    (16-s block at 1024 Hz); wl: another workload (the full 256-s block at 2048 Hz)."""
     from paper_2110_13115_gb300 import inputs
 
-    wl = inputs.tiny()
+    full = wl is not None
+    wl = wl if full else inputs.tiny()
     g = wl.grid
     psd_d = torch.from_numpy(wl.psd).cuda()
     s_hat = api.rb_whiten(api.make_desc(g.fs, g.n, 1, 1, w=1), torch.from_numpy(wl.strain).cuda(), psd_d)
     rng = np.random.default_rng(3)
-    tc = wl.injections[0].tc
-    m = wl.bank[np.arange(n_cand) % len(wl.bank), :2]
+    inj = [wl.injections[i % len(wl.injections)] for i in range(n_cand)]
+    tc = np.array([j.tc for j in inj])
+    # masses: the tiny bank's templates; on another workload each candidate's injection's own masses
+    m = np.array([j.params[:2] for j in inj]) if full else wl.bank[np.arange(n_cand) % len(wl.bank), :2]
     mt = m[:, 0] + m[:, 1]
     eta = m[:, 0] * m[:, 1] / mt ** 2
     mc = mt * eta ** 0.6
@@ -497,7 +501,9 @@ def refine_rate(api, torch, n_cand=1024, steps=20, reps=3):
     ms = e0.elapsed_time(e1) / reps
     return dict(value=n_cand / (ms / 1e3), unit="candidates/s", candidates=n_cand, steps=steps, ms_per_call=ms,
                 mean_J_start=float(J0.mean()), mean_J_refined=float(J.mean()),
-                workload="tiny: 64-template bank, 16-s block at 1024 Hz, one injection")
+                workload=(f"full: {g.n // int(g.fs)}-s block at {g.fs:g} Hz (n = {g.n}), candidates around its "
+                          f"{len(wl.injections)} injections" if full else
+                          "tiny: 64-template bank, 16-s block at 1024 Hz, one injection"))
 
 
 def batch_measure(args, n_segments, steps, warmup, dist=None):
@@ -1155,6 +1161,7 @@ def main():
     if rank == 0 and world == 1:  # after every timed region; a failure here only loses this entry
         try:
             refined = refine_rate(api, torch)
+            refined["full_block"] = refine_rate(api, torch, wl=wl, reps=2)
         except Exception as exc:  # noqa: BLE001
             refined = dict(error=f"{type(exc).__name__}: {exc}"[:300])
         if args.batch_segments > 0:

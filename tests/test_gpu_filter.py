@@ -449,6 +449,47 @@ def test_stage2_tc_bin_groups(api, w, mode):
     compare_triggers(got, ref2, w, 1.5, ref_rho=zr)
 
 
+def test_stage2_tc_many_pieces_per_cta(api):
+    """Hundreds of bin groups with 1 to 700 records each: every CTA of the persistent tcgen05 second
+    stage takes several pieces of one to four tiles, so each tensor-memory slot is reused after pieces
+    that left it idle. The triggers agree with the per-bin mma.sync second stage within its rounding."""
+    from paper_2110_13115_gb300 import _native as N
+
+    lib = N.load()
+    n, k, T, w = 1 << 15, 201, 1200, 8
+    half, nb = n // 2, n // (2 * w)
+    a = _rand_coeff(T, k, 71).astype(np.complex64)
+    beta = inputs.complex_normal((k, half), 72).astype(np.complex64)
+    rng = np.random.default_rng(73)
+    groups = rng.choice(nb // 2, size=600, replace=False)
+    tm, bn = [], []
+    for grp in np.sort(groups):
+        ts = np.sort(rng.choice(T, size=int(rng.integers(1, 701)), replace=False))
+        for t in ts:  # one or both bins of the group, in bin order (a run)
+            for b in ((0,), (1,), (0, 1))[int(rng.integers(0, 3))]:
+                tm.append(t)
+                bn.append(nb + 2 * grp + b)
+    cands = np.zeros(len(tm), dtype=api.CANDIDATE_NP)
+    cands["tmpl"], cands["bin"] = tm, bn
+    d = api.make_desc(1024.0, n, k, T, w=w, rho_ii=2.0, cand_capacity=1 << 20)
+    basis = api.Basis(_dev(np.zeros((k, half), np.complex64)), _dev(a), n)
+    api.rb_pack_coeff(d, basis)
+    outs = []
+    try:
+        for tc in (1, 0):
+            lib.rbx_set_stage2_tc(tc)
+            buf, nt = api.rb_stage2(d, basis, _dev(beta), _dev(cands.view(np.uint8)), len(cands), capacity=1 << 20)
+            outs.append(api.triggers_numpy(buf, nt))
+    finally:
+        lib.rbx_set_stage2_tc(1)
+    got, mma = outs
+    zr = np.abs(np.conj(a.astype(np.complex128)) @ beta.astype(np.complex128))
+    ref = np.zeros(len(mma), dtype=mf.TRIGGER_DTYPE)
+    ref["template"], ref["sample"], ref["snr"], ref["phase"] = mma["tmpl"], mma["sample"], mma["snr"], mma["phase"]
+    stats = compare_triggers(got, ref, w, 2.0, ref_rho=zr)
+    assert stats["both"] > 50000, stats
+
+
 @pytest.mark.parametrize("w", [1, 2, 4, 8])
 @pytest.mark.parametrize("k", [24, 40, 256, 400])
 def test_stage2_tc_parity(api, w, k):
