@@ -44,6 +44,7 @@ struct TcParams {
   int T;          // templates (rows of A = 2T)
   int N;          // valid bins (rows of B)
   int KB;         // K blocks of 64
+  int last_k16;   // 16-wide K steps of the last block that hold data (columns < 2k; the rest is zero)
   int num_m, num_n;
   float thr2;
   int bin0;
@@ -173,8 +174,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a1 = a0 + A_BYTES;
           const uint32_t b0 = a0 + NA * A_BYTES;
           const uint32_t b1 = b0 + B_BYTES;
+          // the zero-padded K steps past 2k in the last block add nothing: skipped
+          const int nkk = kb == p.KB - 1 ? p.last_k16 : BK / 16;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
+            if (kk >= nkk) break;
             const uint32_t off = kk * 32;
             tc_mma(d, sw128_desc(a0 + off), sw128_desc(b0 + off), p.idesc, (kb | kk) != 0);
             if (NB == 2) tc_mma(d, sw128_desc(a0 + off), sw128_desc(b1 + off), p.idesc, 1);
@@ -435,6 +439,7 @@ int build_params(const rb_filter_desc& d, const rb_basis& b, const rb::Geometry&
   p.T = d.n_templates;
   p.N = (int)g.n_bins;
   p.KB = g.kp / BK;
+  p.last_k16 = (2 * d.k - (p.KB - 1) * BK + 15) / 16;  // 1..4
   p.num_m = (int)((M + BM - 1) / BM);
   p.num_n = (int)((g.n_bins + BN - 1) / BN);
   p.thr2 = d.rho_i * d.rho_i;
