@@ -393,11 +393,10 @@ __global__ void __launch_bounds__(256, 3) k_stage2_bins(const __half* __restrict
                                                      unsigned long long* counter, int64_t cap, int tmpl_base) {
   constexpr int NT = S2<W>::NT;
   extern __shared__ __align__(16) uint8_t s2mem[];
-  const int pitch = k16 + 1;                        // padded window rows (bank spread)
   const int nkc = 2 * k16 / 16;                     // K chunks: Re half then Im half (even)
   uint2* frag = reinterpret_cast<uint2*>(s2mem);    // [2][nkc][NT][32]
   uint8_t* region = s2mem + sizeof(uint2) * 2 * nkc * NT * 32;
-  float2* win = reinterpret_cast<float2*>(region);  // [W][pitch] while a bin is staged
+  float2* win = reinterpret_cast<float2*>(region);  // [W][k16 + 1] while a bin is staged
   uint4* ring = reinterpret_cast<uint4*>(region) + (threadIdx.x >> 5) * (D * 4 * 32);  // this warp's slots
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int g = lane >> 2, t4 = lane & 3;
