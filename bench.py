@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-3, help="largest single-template SNR loss of a sub-bank basis")
     p.add_argument("--k-build", type=int, default=320, help="basis vectors built per sub-bank before truncation")
     p.add_argument("--k", type=int, default=None, help="fixed basis size per sub-bank (skips the tolerance)")
+    p.add_argument("--power-iters", type=int, default=1, help="subspace iterations of the randomised basis build")
     p.add_argument("--batch-segments", type=int, default=64,
                    help="segments of the batching workload reported under 'batch' (0: skip it)")
     p.add_argument("--templates", type=int, default=10000)
@@ -654,7 +655,7 @@ def build_subbanks(api, torch, wl, psd_d, args):
         t0 = time.perf_counter()
         kb = min(args.k or args.k_build, len(idx))
         full = api.rb_build(api.Bank(np.ascontiguousarray(wl.bank[idx]), g.fs, g.n, g.f_low, pn), psd_d, kb,
-                            oversample=64, power_iters=1)
+                            oversample=64, power_iters=args.power_iters)
         loss = api.rb_basis_max_loss(full)
         if args.k:
             k = kb
@@ -1188,7 +1189,8 @@ def main():
                         call="rb_filter_banks with desc.mem = RB_MEM_HOST_STRAIN | RB_MEM_HOST_TRIGGERS (pinned host "
                              "strain in, pinned host triggers out, copies inside the call)"),
                gpu_launches=int(launches), clocks=clocks, stage_ms=stage_ms, plain_mf=plain, accuracy=acc,
-               basis=dict(build_s=build_s, tol=args.tol, k_build=args.k_build, oversample=64, power_iters=1,
+               basis=dict(build_s=build_s, tol=args.tol, k_build=args.k_build, oversample=64,
+                          power_iters=args.power_iters,
                           max_truncation_loss=max(sb["max_loss"] for sb in subs),
                           mean_truncation_loss=float(np.mean(np.concatenate([sb["template_loss"] for sb in subs])))),
                refine=refined, batch=batch, n_triggers=int(nt))
