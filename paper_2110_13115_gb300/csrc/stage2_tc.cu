@@ -12,7 +12,7 @@
 // The arg-max over each bin of a record's mask is reported when |z| >= rho_II. Reading a coefficient
 // row once for all of a template's candidate bins of the group cuts the gathers, which bound this
 // kernel, by the number of candidates per record (about 1.8 on clustered candidates at w = 8).
-// Persistent kernel, one CTA per SM, 416 threads, over the pieces (<= 512 records of one group)
+// Persistent kernel, one CTA per SM, 544 threads, over the pieces (<= 512 records of one group)
 // that the bucketing produced:
 //   warps 0-3  : coefficient producers. Per tile of 128 candidates each warp gathers the coefficient
 //                rows of its 32 candidates, K block by K block, with cp.async into an S-deep ring
@@ -23,7 +23,7 @@
 //   warp 4     : tensor-memory allocation and the MMA issuer (one thread), two tiles in flight.
 //   warps 5-8  : epilogue: one tensor-memory lane quarter each; arg-max over each bin of the record's
 //                mask, rho_II, triggers.
-//   warps 9-12 : window producers: the group's B operand (hi and lo windows side by side, 128-byte
+//   warps 9-16 : window producers: the group's B operand (hi and lo windows side by side, 128-byte
 //                swizzled K-major), double-buffered, so a piece's window is built while the one before runs.
 // Every mbarrier wait is bounded (1 s); a timeout sets RB_FLAG_TIMEOUT and every role stops; copies
 // and products in flight are waited for (bounded) and tensor memory is freed before the CTA exits.
@@ -48,7 +48,8 @@ constexpr int kBM = 128;          // candidates per tile (tensor-memory lanes)
 constexpr int kKB = 64;           // K block: 64 FP16 = one 128-byte swizzled row
 constexpr int kMaxStagesA = 6;    // coefficient ring depth, at most
 constexpr int kAStageBytes = 2 * kBM * 128;
-constexpr int kThreadsTc = 416;   // 4 + 1 + 4 + 4 warps
+constexpr int kWinThreads = 256;  // window producers (8 warps)
+constexpr int kThreadsTc = 288 + kWinThreads;  // 4 + 1 + 4 warps, then the window producers
 constexpr unsigned kFull = 0xffffffffu;
 
 struct S2Params {
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
       mbar_init(&aempty[s], 1);
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&bfull[i], 128);
+      mbar_init(&bfull[i], kWinThreads);
       mbar_init(&bempty[i], 1);
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 4);
@@ -349,11 +350,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
     }
   } else {
     // ---------------- window producers: B operand of each piece's bin, double-buffered
-    const int tid = threadIdx.x - 9 * 32;  // 0..127
+    const int tid = threadIdx.x - 9 * 32;  // 0..kWinThreads-1
     // zero both B buffers once: positions >= 2 k16 are never written again
-    for (uint32_t o = tid * 16; o < p.nbuf * b_buf; o += 128 * 16)
+    for (uint32_t o = tid * 16; o < p.nbuf * b_buf; o += kWinThreads * 16)
       *reinterpret_cast<uint4*>(gen + (b0 - base) + o) = make_uint4(0u, 0u, 0u, 0u);
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(kWinThreads) : "memory");
     // one work item: the 16-byte chunk of packed positions 8 ch .. 8 ch + 7 (eight K columns) for
     // sample r, both parts (B rows 2r and 2r + 1), hi and lo: eight beta loads, four 16-byte stores
     const int nchunk = 2 * p.k16 / 8, total = nchunk * S;
@@ -370,11 +371,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
       const int64_t m0 = (int64_t)grp * S;  // valid-half index of the group's first sample
       uint8_t* bt = gen + (b0 - base) + pb * b_buf;
       constexpr int U = 2;
-      for (int i0 = tid; i0 < total; i0 += U * 128) {
+      for (int i0 = tid; i0 < total; i0 += U * kWinThreads) {
         float2 bv[U][8];
 #pragma unroll
         for (int u = 0; u < U; ++u) {  // loads first, then the stores (zero past the valid half)
-          const int idx = i0 + u * 128, ch = idx / S, r = idx - ch * S;
+          const int idx = i0 + u * kWinThreads, ch = idx / S, r = idx - ch * S;
           const bool in = idx < total && m0 + r < p.half;
 #pragma unroll
           for (int sl = 0; sl < 8; ++sl) {
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_stage2_tc(S2Params p) {
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const int idx = i0 + u * 128, ch = idx / S, r = idx - ch * S;
+          const int idx = i0 + u * kWinThreads, ch = idx / S, r = idx - ch * S;
           if (idx >= total) break;
           const int q = ch >> 2, t4 = ch & 3;
           uint32_t h[2][4], l[2][4];  // [part][pair of halves]
