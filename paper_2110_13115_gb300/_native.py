@@ -146,6 +146,7 @@ HOST_HOOKS = {
     "rbx_stage2_withhold_copies": (C.c_int, [C.c_int]),
     "rbx_set_fft_radix32": (C.c_int, [C.c_int]),
     "rbx_set_stage2_ring": (C.c_int, [C.c_int]),
+    "rbx_set_stage2_tc_piece": (C.c_int, [C.c_int]),
     "rbx_set_stage2_tc_windows": (C.c_int, [C.c_int]),
     "rbx_mma_sync_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
 }

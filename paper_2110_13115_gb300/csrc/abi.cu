@@ -178,8 +178,8 @@ void carve(const rb_filter_desc& d, const Geometry& g, char* base, Workspace* ws
     ws->cand_sorted = (SortedCand*)take(sizeof(SortedCand) * (size_t)std::max<int64_t>(d.cand_capacity, 1));
     ws->bin_count = (unsigned*)take(sizeof(unsigned) * (size_t)(g.n_bins + 1));
     ws->bin_start = (unsigned*)take(sizeof(unsigned) * (size_t)(g.n_bins + 1));
-    // pieces: sum over bins of ceil(c_b / kStage2Piece) <= n_bins + capacity / kStage2Piece
-    ws->pieces = (int4*)take(sizeof(int4) * (size_t)(g.n_bins + d.cand_capacity / kStage2Piece + 1));
+    // pieces: sum over groups of ceil(c_g / piece) <= n_bins + capacity / kStage2MinPiece
+    ws->pieces = (int4*)take(sizeof(int4) * (size_t)(g.n_bins + d.cand_capacity / kStage2MinPiece + 1));
     ws->piece_total = (unsigned*)take(sizeof(unsigned));
   }
   ws->total = off;

@@ -12,6 +12,7 @@ namespace rb {
 
 // Second-stage work item: at most this many bucketed candidates of one bin.
 constexpr unsigned kStage2Piece = 512;
+constexpr unsigned kStage2MinPiece = 128;  // the smallest work piece any second stage asks for
 
 struct Geometry {
   int64_t n = 0;       // block length

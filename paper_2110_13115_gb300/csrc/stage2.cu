@@ -35,6 +35,10 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kPiece = rb::kStage2Piece;  // candidates per second-stage work item
 std::atomic<int> g_stage2_ring{2};  // coefficient ring slots of the mma.sync second stage (0: registers)
+// records per work piece of the tcgen05 second stage: 256 (two tiles) balances the persistent CTAs'
+// grid-stride walk over the pieces better than 512 at the cost of more window builds (0.539 against
+// 0.565 ms on the 10,000-template block; 128: 0.531 ms but a slower scan)
+std::atomic<int> g_tc_piece{256};
 
 // Bucketing works on chunks of consecutive candidates. The first stage emits candidates in tile
 // order and the tiles in flight share their bins, so a chunk's bins lie in a narrow range: each CTA
@@ -132,7 +136,8 @@ constexpr size_t kScanSmem = 2 * sizeof(unsigned) * (spad(kScanTile) + 1);
 // piece prefix. Also raises
 // RB_FLAG_CAND_OVERFLOW when the first stage found more candidates than the buffer holds.
 __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count, unsigned* __restrict__ start, int nb,
-                                                   int4* __restrict__ pieces, unsigned* __restrict__ piece_total,
+                                                   unsigned piece, int4* __restrict__ pieces,
+                                                   unsigned* __restrict__ piece_total,
                                                    const unsigned long long* dev_count, int64_t cap,
                                                    unsigned* flags) {
   using u64 = unsigned long long;
@@ -142,7 +147,7 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
   __shared__ u64 wsum[32];
   __shared__ u64 carry_s, carry_next;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  auto packed = [](unsigned c) { return (u64)c | ((u64)((c + kPiece - 1) / kPiece) << 32); };
+  auto packed = [piece](unsigned c) { return (u64)c | ((u64)((c + piece - 1) / piece) << 32); };
   if (tid == 0) {
     carry_s = 0;
     if (*dev_count > (u64)cap) atomicOr(flags, (unsigned)RB_FLAG_CAND_OVERFLOW);
@@ -216,8 +221,8 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
         if (pp_s[spad(mid)] <= pi) lo = mid;
         else hi = mid;
       }
-      const unsigned c0 = st_s[spad(lo)] + (pi - pp_s[spad(lo)]) * kPiece;
-      const unsigned c1 = min(st_s[spad(lo + 1)], c0 + kPiece);
+      const unsigned c0 = st_s[spad(lo)] + (pi - pp_s[spad(lo)]) * piece;
+      const unsigned c1 = min(st_s[spad(lo + 1)], c0 + piece);
       pieces[pi] = make_int4(base + lo, (int)c0, (int)c1, 0);
     }
     __syncthreads();
@@ -585,8 +590,11 @@ int stage2_bucket(const rb_filter_desc& d, const Geometry& g, const Workspace& w
                                        ws.bin_count);
   RB_LAUNCH_CHECK();
   RB_CUDA_TRY(cudaFuncSetAttribute(k_bin_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem));
-  k_bin_scan<<<1, 1024, kScanSmem, st>>>(ws.bin_count, ws.bin_start, ng, ws.pieces, ws.piece_total, ws.cand_count,
-                                         d.cand_capacity, ws.flags);
+  // work pieces: kStage2Piece records per group at most; the tcgen05 kernel builds one window per piece
+  // and takes pieces of g_tc_piece records
+  const unsigned piece = G > 1 ? (unsigned)g_tc_piece.load() : kPiece;
+  k_bin_scan<<<1, 1024, kScanSmem, st>>>(ws.bin_count, ws.bin_start, ng, piece, ws.pieces, ws.piece_total,
+                                         ws.cand_count, d.cand_capacity, ws.flags);
   RB_LAUNCH_CHECK();
   k_bin_scatter<<<152 * 8, 256, 0, st>>>(ws.cand, ws.cand_count, d.cand_capacity, bin0, bin_lo, nb, gs,
                                          ws.bin_start, ws.bin_count, ws.cand_sorted);
@@ -696,4 +704,13 @@ extern "C" int rbx_mma_sync_rate(int iters, double* per_s) {
   if (e1) cudaEventDestroy(e1);
   if (out) cudaFree(out);
   return rc;
+}
+
+// Host-only hook (not part of the C ABI): records per work piece of the tcgen05 second stage, a
+// multiple of 128 from rb::kStage2MinPiece up to 4096 (each piece costs one group-window build).
+// RB_ERR_BAD_INPUT otherwise.
+extern "C" int rbx_set_stage2_tc_piece(int records) {
+  if (records < (int)rb::kStage2MinPiece || records > 4096 || records % 128) return RB_ERR_BAD_INPUT;
+  g_tc_piece.store(records);
+  return 0;
 }

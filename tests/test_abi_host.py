@@ -111,7 +111,7 @@ def test_plan_validation(lib):
 
 def test_workspace_per_candidate(lib):
     """Each unit of cand_capacity costs a 16-byte candidate, a 12-byte bucketed (template, block, bin
-    mask) record and 1/512 of a 16-byte work piece (buffers are 256-byte aligned). The plan is the larger
+    mask) record and 1/128 of a 16-byte work piece (buffers are 256-byte aligned). The plan is the larger
     of the hierarchical and the template-method carvings: from 2^20 candidates on, the hierarchical one."""
     from paper_2110_13115_gb300 import _native as N
     from paper_2110_13115_gb300.api import make_desc
@@ -124,7 +124,7 @@ def test_workspace_per_candidate(lib):
 
     c0, extra = 1 << 20, 512 * 4096
     grow = ws(c0 + extra) - ws(c0)
-    expect = extra * (16 + 12) + extra // 512 * 16
+    expect = extra * (16 + 12) + extra // 128 * 16
     assert abs(grow - expect) <= 3 * 256, (grow, expect)
     d = make_desc(fs=1024.0, n=16384, k=16, n_templates=64, w=8, cand_capacity=1 << 31)
     out = N.rb_filter_sizes()
