@@ -10,10 +10,10 @@
 // tensor memory: the split terms hi.hi + hi.lo + lo.hi (+ lo.lo), FP32-accurate.
 //
 // The arg-max over each bin of a record's mask is reported when |z| >= rho_II. Reading a coefficient
-// row once for all of a template's candidate bins of the group cuts the gathers, which bound this
-// kernel, by the number of candidates per record (about 1.8 on clustered candidates at w = 8).
-// Persistent kernel, one CTA per SM, 544 threads, over the pieces (<= 512 records of one group)
-// that the bucketing produced:
+// row once for all of a template's candidate bins of the group cuts the gathers by the number of
+// candidates per record (about 1.8 on clustered candidates at w = 8).
+// Persistent kernel, one CTA per SM, 544 threads, over the pieces (up to 256 records of one group by
+// default, dealt round-robin to the CTAs) that the bucketing produced:
 //   warps 0-3  : coefficient producers. Per tile of 128 candidates each warp gathers the coefficient
 //                rows of its 32 candidates, K block by K block, with cp.async into an S-deep ring
 //                (S = 2..6, as many 32-KB stages as shared memory holds); a stage is published to the
@@ -28,9 +28,10 @@
 // Every mbarrier wait is bounded (1 s); a timeout sets RB_FLAG_TIMEOUT and every role stops; copies
 // and products in flight are waited for (bounded) and tensor memory is freed before the CTA exits.
 //
-// What bounds the kernel is the round trip of a ring stage (coefficient gather from L2, then the
-// products' completion) against the shared memory left for the ring (three 32-KB stages beside the
-// two 56-KB windows at k <= 256).
+// Neither the tensor pipe nor L2 is saturated (about a fifth of each on the 10,000-template block):
+// the pace is set by the balance of the CTAs' walk over the pieces and by the window builds (one per
+// piece), the gathers' round trips through the ring (three 32-KB stages beside the two 56-KB windows
+// at k <= 256) overlapping them.
 #include <cuda_fp16.h>
 
 #include <algorithm>
