@@ -136,3 +136,30 @@ def test_null_arguments_rejected_without_gpu(lib):
 
     assert lib.rb_filter_plan(None, None) == N.RB_ERR_BAD_INPUT
     assert b"NULL" in lib.rb_last_error_detail()
+
+
+def test_second_stage_hooks_validate_without_gpu(lib):
+    """The host-only second-stage hooks check their arguments on the host (no CUDA call) and leave the
+    defaults in place: tcgen05 kernel on, two-slot mma.sync ring, 256-record tcgen05 pieces."""
+    from paper_2110_13115_gb300 import _native as N
+
+    for bad in (2, 7, 32 + 1, -1):
+        assert lib.rbx_set_stage2_tc(bad) == N.RB_ERR_BAD_INPUT
+    for bad in (1, 5, -2):
+        assert lib.rbx_set_stage2_ring(bad) == N.RB_ERR_BAD_INPUT
+    for bad in (0, 64, 100, 300, 4224, 8192):
+        assert lib.rbx_set_stage2_tc_piece(bad) == N.RB_ERR_BAD_INPUT
+    for bad in (-1, 3):
+        assert lib.rbx_set_stage2_tc_windows(bad) == N.RB_ERR_BAD_INPUT
+    try:
+        for ok in (128, 384, 4096):
+            assert lib.rbx_set_stage2_tc_piece(ok) == 0
+        for ok in (0, 16, 32, 1):
+            assert lib.rbx_set_stage2_tc(ok) == 0
+        for ok in (0, 3, 4, 2):
+            assert lib.rbx_set_stage2_ring(ok) == 0
+    finally:
+        lib.rbx_set_stage2_tc_piece(256)
+        lib.rbx_set_stage2_tc(1)
+        lib.rbx_set_stage2_ring(2)
+        lib.rbx_set_stage2_tc_windows(0)
