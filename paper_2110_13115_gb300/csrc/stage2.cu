@@ -41,11 +41,12 @@ std::atomic<int> g_stage2_ring{2};  // coefficient ring slots of the mma.sync se
 std::atomic<int> g_tc_piece{256};
 
 // Bucketing works on chunks of consecutive candidates. The first stage emits candidates in tile
-// order and the tiles in flight share their bins, so a chunk's bins lie in a narrow range: each CTA
-// histograms its chunk in shared memory over a window of kWin bins from the chunk's smallest bin and
-// then issues one global atomic per (chunk, bin) instead of one per candidate. Bins outside the
-// window (candidate lists in any other order) take one global atomic each.
-constexpr int kWin = 4096;  // histogram window (bins)
+// order and the tiles in flight share their bins, so a chunk's groups lie in a narrow range: each CTA
+// histograms its chunk in shared memory over a window of kWin groups from the chunk's smallest group
+// and then issues one global atomic per (chunk, group) instead of one per candidate. Groups outside
+// the window (candidate lists in any other order) take one global atomic each. Small chunks (1024
+// candidates in the count, 512 in the scatter) keep most CTAs of the grid busy on ~10^6 candidates.
+constexpr int kWin = 1024;  // histogram window (groups)
 
 __device__ __forceinline__ int block_min(int v, int* red) {  // blockDim.x == 256
   v = __reduce_min_sync(kFull, v);
@@ -75,11 +76,11 @@ __device__ __forceinline__ bool run_head(const rb_candidate* __restrict__ cand, 
 
 // Per-group record counts (groups of 2^gs bins) of the candidates [0, min(cap, count)) whose bin
 // (relative to bin0) lies in [blo, nb): bins before blo are dropped, as a block whose earlier valid
-// samples another block already covers keeps only [blo, nb). 256 threads, chunks of 4096 candidates.
+// samples another block already covers keeps only [blo, nb). 256 threads, chunks of 1024 candidates.
 __global__ void __launch_bounds__(256) k_bin_count(const rb_candidate* __restrict__ cand,
                                                    const unsigned long long* dev_count, int64_t cap, int bin0,
                                                    int blo, int nb, int gs, unsigned* __restrict__ count) {
-  constexpr int PER = 16, CHUNK = 256 * PER;
+  constexpr int PER = 4, CHUNK = 256 * PER;
   __shared__ unsigned hist[kWin];
   __shared__ int red[8];
   const int64_t n = (int64_t)min((unsigned long long)cap, *dev_count);
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(1024) k_bin_scan(unsigned* __restrict__ count,
   }
 }
 
-// Records into group order, by chunks of 2048 candidates (256 threads): each run head gathers its
+// Records into group order, by chunks of 512 candidates (256 threads): each run head gathers its
 // run's bin mask (at most 2^gs following candidates); a record's rank among the chunk's records of
 // its group comes from a shared-memory atomic, the chunk's base in the group from one global cursor
 // atomic per (chunk, group); groups outside the window take one global atomic each.
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const rb_candidate* __restr
                                                      int blo, int nb, int gs, const unsigned* __restrict__ start,
                                                      unsigned* __restrict__ cursor,
                                                      rb::SortedCand* __restrict__ out) {
-  constexpr int PER = 8, CHUNK = 256 * PER;
+  constexpr int PER = 2, CHUNK = 256 * PER;
   __shared__ unsigned hist[kWin];
   __shared__ int red[8];
   const int64_t n = (int64_t)min((unsigned long long)cap, *dev_count);

@@ -334,11 +334,11 @@ def test_stage2_coefficient_ring_depths(api, w):
 
 
 def test_bucketing_window_and_fallback(api):
-    """Bucketing histograms each chunk of consecutive candidates over a 4096-bin window from the
-    chunk's smallest bin; bins beyond it take the per-candidate path. With 8192 valid bins, candidates
-    in bin order keep every chunk inside its window, a random order sends about half of each chunk's
-    candidates down the other path: both orders give bit-identical triggers, which agree with the
-    oracle."""
+    """Bucketing histograms each chunk of consecutive candidates over a 1024-group window from the
+    chunk's smallest group; groups beyond it take the per-candidate path. With 8192 valid bins (4096
+    groups of two for the tcgen05 second stage), candidates in bin order keep every chunk inside its
+    window, a random order sends about three quarters of each chunk's candidates down the other path:
+    both orders give bit-identical triggers, which agree with the oracle."""
     n, k, T, w = 1 << 17, 24, 2000, 8
     half, nb = n // 2, n // (2 * w)
     assert nb == 8192
