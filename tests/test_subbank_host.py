@@ -115,3 +115,29 @@ def test_k_for_loss_errors(api):
     with pytest.raises(N.RBError) as e:
         api.rb_bank_tau0(_bank([(1.0, -1.0, 0, 0)]), 30.0)
     assert e.value.code == N.RB_ERR_BAD_INPUT
+
+
+def test_banks_plan_shares_one_workspace(api):
+    """rb_banks_plan (host only): the workspace of the largest sub-bank, the host trigger staging region
+    only when the descriptors ask for host triggers (at an n-only offset, so every sub-bank finds it in
+    place), and descriptors that differ in n, w or mem are rejected."""
+    from paper_2110_13115_gb300 import _native as N
+
+    fs, n = 2048.0, 1 << 19
+    ds = [api.make_desc(fs, n, k, 2500, w=8, precision="fp16_split_a", cand_capacity=1 << 22) for k in (201, 106, 85)]
+    one = [api.rb_filter_plan(d).workspace_bytes for d in ds]
+    plan = api.rb_banks_plan(ds)
+    assert plan.workspace_bytes == max(one)
+    assert plan.host_trig_capacity == (96 << 20) // 24
+    hs = [N.rb_filter_desc.from_buffer_copy(d) for d in ds]
+    for h in hs:
+        h.mem = N.RB_MEM_HOST_STRAIN | N.RB_MEM_HOST_TRIGGERS
+    assert api.rb_banks_plan(hs).workspace_bytes == plan.workspace_bytes + (96 << 20)
+    odd = N.rb_filter_desc.from_buffer_copy(ds[1])
+    odd.w = 4
+    with pytest.raises(N.RBError):
+        api.rb_banks_plan([ds[0], odd])
+    odd = N.rb_filter_desc.from_buffer_copy(ds[1])
+    odd.mem = N.RB_MEM_HOST_TRIGGERS
+    with pytest.raises(N.RBError):
+        api.rb_banks_plan([ds[0], odd])
