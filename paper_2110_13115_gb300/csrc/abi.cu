@@ -883,12 +883,17 @@ int rb_filter_banks(const rb_filter_desc* descs, const rb_basis* bases, int32_t 
   // past their own count
   cudaStream_t cs = nullptr;
   std::vector<cudaEvent_t> done;
+  // on every return: the copies into the caller's host buffer have landed (an early error return
+  // included), then the events go
   struct EventGuard {
     std::vector<cudaEvent_t>& ev;
+    cudaStream_t& cs;
     ~EventGuard() {
-      for (cudaEvent_t e : ev) cudaEventDestroy(e);
+      if (cs) cudaStreamSynchronize(cs);
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
     }
-  } guard{done};
+  } guard{done, cs};
   if (host_out) {
     if ((rc = copy_stream(&cs))) return rc;
     done.resize(n_banks, nullptr);
